@@ -1,0 +1,201 @@
+"""Model problems (sparse matrices in CSR) and right-hand sides.
+
+All matrices are square CSR with int32 row pointers and column indices (sorted
+ascending within each row, no duplicates) and float64 values.  Unknowns of a
+d-dimensional grid with side m are the interior nodes, numbered
+lexicographically: i + m*(j + m*k).  Homogeneous Dirichlet neighbours are
+eliminated (their columns are dropped), so a 7-point 3D stencil on m^3 nodes
+has 7*m^3 - 6*m^2 nonzeros: 23,490,000 for m = 150, the figure Sec. 4.1 of the
+paper gives for its Poisson benchmark.  Mesh-size scaling (1/h^2) is omitted:
+it multiplies A by a constant and does not change x for f = A u*.
+
+Stream numbers used with ``gen.rng``: 1 cell coefficients, 2 anisotropy mask,
+3 velocity / Peclet number, 4 diagonal shift, 10 solution vector u*, 11 direct
+right-hand sides.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .rng import uniform01
+
+STREAM_COEF = 1
+STREAM_ANISO = 2
+STREAM_VEL = 3
+STREAM_SHIFT = 4
+STREAM_USTAR = 10
+STREAM_RHS = 11
+
+
+@dataclass
+class Csr:
+    n: int
+    row_ptr: np.ndarray  # int32, n+1
+    col: np.ndarray      # int32, nnz
+    val: np.ndarray      # float64, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n))
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        d[rows, self.col] = self.val
+        return d
+
+
+def poisson3d_nnz(m: int) -> int:
+    """nnz of the 7-point stencil with eliminated Dirichlet neighbours."""
+    return 7 * m ** 3 - 6 * m ** 2
+
+
+def _assemble(n: int, offsets, cols_list, vals_list, mask_list) -> Csr:
+    """Pack per-row neighbour slots (already in ascending column order) into CSR."""
+    cols = np.stack(cols_list, axis=1)
+    vals = np.stack(vals_list, axis=1)
+    mask = np.stack(mask_list, axis=1)
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2 ** 31:
+        raise ValueError("problem too large for int32 row pointers")
+    col = cols[mask].astype(np.int32)
+    val = vals[mask].astype(np.float64)
+    return Csr(n, row_ptr.astype(np.int32), col, val)
+
+
+def _grid3(m: int):
+    idx = np.arange(m ** 3, dtype=np.int64)
+    i = idx % m
+    j = (idx // m) % m
+    k = idx // (m * m)
+    return idx, i, j, k
+
+
+def poisson3d(m: int) -> Csr:
+    """7-point -Laplacian on an m^3 interior grid: diagonal 6, -1 per in-grid neighbour."""
+    n = m ** 3
+    idx, i, j, k = _grid3(m)
+    offs = [-m * m, -m, -1, 0, 1, m, m * m]
+    masks = [k > 0, j > 0, i > 0, np.ones(n, bool), i < m - 1, j < m - 1, k < m - 1]
+    cols = [idx + o for o in offs]
+    vals = [np.full(n, -1.0) if o != 0 else np.full(n, 6.0) for o in offs]
+    return _assemble(n, offs, cols, vals, masks)
+
+
+def poisson2d_shift(m: int, sigma: float) -> Csr:
+    """5-point -Laplacian on an m^2 interior grid with diagonal 4 + sigma."""
+    n = m * m
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % m
+    j = idx // m
+    offs = [-m, -1, 0, 1, m]
+    masks = [j > 0, i > 0, np.ones(n, bool), i < m - 1, j < m - 1]
+    cols = [idx + o for o in offs]
+    vals = [np.full(n, -1.0) if o != 0 else np.full(n, 4.0 + sigma) for o in offs]
+    return _assemble(n, offs, cols, vals, masks)
+
+
+def varcoef3d(m: int, seed: int, log10_range=(-3.0, 3.0), aniso_frac=0.1, aniso_z=0.01) -> Csr:
+    """Cell-centred finite-volume diffusion with per-cell coefficient.
+
+    k_c = 10^U(lo, hi) per cell; on a Bernoulli(aniso_frac) subset of cells the
+    z-direction coefficient is aniso_z * k_c (anisotropy 1:1:aniso_z).  The face
+    coefficient between cells a and b in direction d is the harmonic mean
+    2 k_a k_b / (k_a + k_b) of their d-coefficients; a boundary face carries
+    2 k_c (Dirichlet value at the face, half a cell away).  Off-diagonals are
+    minus the face coefficients, the diagonal is the sum of all six faces.
+    """
+    n = m ** 3
+    idx, i, j, k = _grid3(m)
+    lo, hi = log10_range
+    kc = 10.0 ** (lo + (hi - lo) * uniform01(seed, STREAM_COEF, n))
+    aniso = uniform01(seed, STREAM_ANISO, n) < aniso_frac
+    kd = [kc, kc, np.where(aniso, aniso_z * kc, kc)]  # x, y, z coefficients
+
+    def face(d, nb):
+        a = kd[d]
+        b = kd[d][np.clip(nb, 0, n - 1)]
+        return 2.0 * a * b / (a + b)
+
+    # neighbours in ascending column order: z-, y-, x-, diag, x+, y+, z+
+    spec = [(2, -m * m, k > 0), (1, -m, j > 0), (0, -1, i > 0),
+            None, (0, 1, i < m - 1), (1, m, j < m - 1), (2, m * m, k < m - 1)]
+    cols, vals, masks = [], [], []
+    diag = np.zeros(n)
+    for s in spec:
+        if s is None:
+            cols.append(idx)
+            vals.append(None)
+            masks.append(np.ones(n, bool))
+            continue
+        d, o, inside = s
+        nb = idx + o
+        f = np.where(inside, face(d, nb), 2.0 * kd[d])
+        diag += f
+        cols.append(nb)
+        vals.append(-f)
+        masks.append(inside)
+    vals[3] = diag
+    return _assemble(n, None, cols, vals, masks)
+
+
+def convdiff3d(m: int, seed: int, pe_range=(1.0, 100.0)):
+    """Upwind convection-diffusion: 7-point diffusion plus first-order upwinding.
+
+    Velocity v is a seeded unit vector (uniform on the sphere), the cell Peclet
+    number Pe ~ U(pe_range).  For each axis d with c_d = Pe*|v_d|, c_d is added
+    to the diagonal and -c_d to the coefficient of the upwind neighbour (the one
+    at -sign(v_d)); an upwind neighbour outside the grid is eliminated like the
+    Dirichlet neighbours.  The result is a nonsymmetric M-matrix.
+    Returns (Csr, v, Pe).
+    """
+    n = m ** 3
+    idx, i, j, k = _grid3(m)
+    u = uniform01(seed, STREAM_VEL, 3)
+    z = 2.0 * u[0] - 1.0
+    phi = 2.0 * np.pi * u[1]
+    r = np.sqrt(max(0.0, 1.0 - z * z))
+    v = np.array([r * np.cos(phi), r * np.sin(phi), z])
+    pe = pe_range[0] + (pe_range[1] - pe_range[0]) * u[2]
+    c = pe * np.abs(v)
+    offs = [-m * m, -m, -1, 0, 1, m, m * m]
+    axis = [2, 1, 0, None, 0, 1, 2]
+    masks = [k > 0, j > 0, i > 0, np.ones(n, bool), i < m - 1, j < m - 1, k < m - 1]
+    cols = [idx + o for o in offs]
+    vals = []
+    for o, d in zip(offs, axis):
+        if d is None:
+            vals.append(np.full(n, 6.0 + c.sum()))
+            continue
+        upwind = (o < 0) == (v[d] > 0)  # o<0 is the minus neighbour
+        vals.append(np.full(n, -1.0 - (c[d] if upwind else 0.0)))
+    return _assemble(n, offs, cols, vals, masks), v, pe
+
+
+def uniform_pm1(seed: int, stream: int, count: int) -> np.ndarray:
+    """U(-1, 1) doubles: 2u - 1 with 53-bit u."""
+    return 2.0 * uniform01(seed, stream, count) - 1.0
+
+
+def rhs_from_solution(A: Csr, seed: int):
+    """Seeded u* ~ U(-1,1) and f = A u* (input construction; returns (f, u*))."""
+    ustar = uniform_pm1(seed, STREAM_USTAR, A.n)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    f = np.bincount(rows, weights=A.val * ustar[A.col], minlength=A.n)
+    return f, ustar
+
+
+def batched_sides(count: int, seed: int, lo: int = 16, hi: int = 128):
+    """Per-system grid sides n ~ U{lo..hi} and shifts sigma ~ U(0, 0.1)."""
+    u = uniform01(seed, STREAM_COEF, count)
+    sides = lo + np.minimum((u * (hi - lo + 1)).astype(np.int64), hi - lo)
+    sigma = 0.1 * uniform01(seed, STREAM_SHIFT, count)
+    return sides, sigma
+
+
+def serving_sides(count: int, seed: int, lo: int = 20, hi: int = 160):
+    """Per-request grid sides, log-uniform on [lo, hi] (so unknowns log-uniform too)."""
+    u = uniform01(seed, STREAM_COEF, count)
+    return np.rint(np.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * u)).astype(np.int64)

@@ -1,0 +1,807 @@
+/*
+ * amg_oracle.c -- plain, slow, FP64 CPU oracle of smoothed-aggregation AMG
+ * preconditioned CG / BiCGStab.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference for the
+ * CUDA library in paper_1811_05704_gb300/.  Only tests/, the smoke check in
+ * __graft_entry__.py and bench.py's CPU-baseline leg may load it.  It shares
+ * no code, header, table or helper with the CUDA path, and the CUDA path never
+ * calls it.
+ *
+ * What it computes follows the paper (D. Demidov, "AMGCL: an Efficient,
+ * Flexible, and Extensible Algebraic Multigrid Implementation"):
+ *   - Algorithm 1 (AMG setup): while A_i is too big, build P_i and R_i and the
+ *     Galerkin operator A_{i+1} = R_i A_i P_i; then a direct solver for A_L.
+ *   - Sec. 2, after Algorithm 1: restriction R = P^T.
+ *   - Algorithm 2 (AMG solve), one V-cycle used as the preconditioner
+ *     (Sec. 2, last paragraph).
+ *   - Sec. 3 "Coarsening strategies": smoothed aggregation (Vanek, Mandel,
+ *     Brezina 1996); "Relaxation methods": damped Jacobi and SPAI-0;
+ *     "Iterative solvers": CG and BiCGStab.
+ * The paper does not spell out the internals of smoothed aggregation, the
+ * smoothers or the Krylov loops; each place where this file commits to a
+ * reading is marked READING and the same reading is listed in the project's
+ * design notes.  The CUDA library implements the same readings in its own
+ * code.
+ *
+ * Pins: every function here is checked in tests/test_oracle_pins.py against
+ * closed forms, invariants, dense linear algebra (numpy) on tiny inputs or
+ * hand-derived values; none is "parity unpinned".
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
+ * integer decisions that depend on floating point -- strength of connection,
+ * the pass-2 argmax of aggregation -- are reproducible bit for bit).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* status codes (same numbering as the library's public header) */
+enum { O_OK = 0, O_INVALID = 1, O_OOM = 2, O_NOT_CONVERGED = 4, O_BREAKDOWN = 5,
+       O_STALLED = 6, O_TOO_LARGE = 7 };
+
+typedef struct {
+    int64_t nrows, ncols;
+    int64_t *ptr; /* nrows + 1 */
+    int32_t *col; /* sorted ascending per row */
+    double *val;
+} ocsr;
+
+typedef struct {
+    double eps_strong;     /* strength threshold at the finest level (0.08) */
+    int eps_halving;       /* 1: eps_l = eps_strong * 0.5^l (Vanek et al. 1996) */
+    int smoother;          /* 0 damped Jacobi, 1 SPAI-0 */
+    double jacobi_omega;   /* 0.72 */
+    int npre, npost;       /* sweeps (1, 1) */
+    int coarse_enough;     /* stop coarsening at <= this many rows (500) */
+    int max_levels;        /* 25 */
+    int max_coarse_dense;  /* largest coarsest level solved densely (4096) */
+} oparams;
+
+typedef struct {
+    ocsr A, P, R;     /* P, R unused on the coarsest level */
+    int32_t *agg;     /* aggregate id of each row (non-coarsest levels) */
+    int64_t nagg;
+    double omega_p;   /* prolongation smoothing weight used on this level */
+    double *d;        /* smoother diagonal */
+    double *f, *x, *t;
+} olevel;
+
+#define OMAXLEV 64
+typedef struct {
+    int nlev;
+    olevel lev[OMAXLEV];
+    int64_t nc;       /* coarsest size */
+    double *lu;       /* row-major LU factors of A_L, unit lower L */
+    int64_t *piv;     /* row permutation: piv[k] = original row at position k */
+    double *work;     /* Krylov work vectors */
+} ohier;
+
+/* ------------------------------------------------------------------ helpers */
+
+static void csr_free(ocsr *a) {
+    free(a->ptr); free(a->col); free(a->val);
+    a->ptr = NULL; a->col = NULL; a->val = NULL;
+}
+
+static int csr_alloc(ocsr *a, int64_t nrows, int64_t ncols, int64_t nnz) {
+    a->nrows = nrows; a->ncols = ncols;
+    a->ptr = (int64_t *)calloc((size_t)(nrows + 1), sizeof(int64_t));
+    a->col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    a->val = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    return (a->ptr && a->col && a->val) ? O_OK : O_OOM;
+}
+
+static double diag_entry(const ocsr *a, int64_t i) {
+    for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k)
+        if (a->col[k] == i) return a->val[k];
+    return 0.0;
+}
+
+/* y = A x, each row summed left to right */
+static void spmv(const ocsr *a, const double *x, double *y) {
+    for (int64_t i = 0; i < a->nrows; ++i) {
+        double s = 0.0;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) s += a->val[k] * x[a->col[k]];
+        y[i] = s;
+    }
+}
+
+static double dot(int64_t n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* ------------------------------------------------- S1 strength of connection
+ * READING (Vanek, Mandel, Brezina 1996, cited in Sec. 3 "Coarsening
+ * strategies"): j != i is a strong neighbour of i iff
+ *     a_ij^2 > eps^2 * |a_ii * a_jj|,
+ * tested on row i only (the relation may be asymmetric for nonsymmetric A).
+ */
+static int is_strong(double aij, double aii, double ajj, double eps2) {
+    return aij * aij > eps2 * fabs(aii * ajj);
+}
+
+/* ---------------------------------------------------- S2 plain aggregation
+ * READING (Vanek-style, fully ordered):
+ *   pass 0: a node with no strong neighbour is its own (singleton) aggregate;
+ *   pass 1: for i ascending, if i and all its strong neighbours are free, the
+ *           set {i} + N_i becomes a new aggregate;
+ *   pass 2: each still-free i joins the aggregate, as of the end of pass 1, of
+ *           the strong neighbour j with the largest |a_ij|/sqrt(|a_ii a_jj|)
+ *           (ties: smallest j);
+ *   pass 3: for i ascending, a still-free i forms a new aggregate with its free
+ *           strong neighbours.
+ * Aggregate ids are numbered in creation order.  Returns the count.
+ */
+static int64_t aggregate(const ocsr *a, const double *diag, double eps, int32_t *agg) {
+    const int64_t n = a->nrows;
+    const double eps2 = eps * eps;
+    int64_t nagg = 0;
+    for (int64_t i = 0; i < n; ++i) agg[i] = -1;
+
+    /* pass 0 */
+    for (int64_t i = 0; i < n; ++i) {
+        int has = 0;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j != i && is_strong(a->val[k], diag[i], diag[j], eps2)) { has = 1; break; }
+        }
+        if (!has) agg[i] = (int32_t)nagg++;
+    }
+    /* pass 1 */
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        int ok = 1;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1] && ok; ++k) {
+            int64_t j = a->col[k];
+            if (j != i && is_strong(a->val[k], diag[i], diag[j], eps2) && agg[j] >= 0) ok = 0;
+        }
+        if (!ok) continue;
+        agg[i] = (int32_t)nagg;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j != i && is_strong(a->val[k], diag[i], diag[j], eps2)) agg[j] = (int32_t)nagg;
+        }
+        ++nagg;
+    }
+    /* pass 2, against a snapshot of the pass-0/1 assignment */
+    int32_t *snap = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!snap) return -1;
+    memcpy(snap, agg, (size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i) {
+        if (snap[i] >= 0) continue;
+        double best = -1.0;
+        int32_t choice = -1;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j == i || snap[j] < 0) continue;
+            if (!is_strong(a->val[k], diag[i], diag[j], eps2)) continue;
+            double c = fabs(a->val[k]) / sqrt(fabs(diag[i] * diag[j]));
+            if (c > best) { best = c; choice = snap[j]; }
+        }
+        if (choice >= 0) agg[i] = choice;
+    }
+    free(snap);
+    /* pass 3 */
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] >= 0) continue;
+        agg[i] = (int32_t)nagg;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j != i && agg[j] < 0 && is_strong(a->val[k], diag[i], diag[j], eps2))
+                agg[j] = (int32_t)nagg;
+        }
+        ++nagg;
+    }
+    return nagg;
+}
+
+/* --------------------------------------------- S3/S4 smoothed prolongation
+ * Tentative P (S3): P_t(i, agg(i)) = 1/sqrt(|agg(i)|) -- unit-norm columns,
+ * the constant vector as near-null space.
+ *
+ * READING (S4): filtered matrix A_F keeps the diagonal and the strong entries
+ * of each row; the weak ones are lumped into the diagonal,
+ *     aF_ii = a_ii - sum_{weak j, ascending} a_ij.
+ * Spectral estimate rho = max_i sum_{j in row of A_F, ascending} |aF_ij| / |aF_ii|
+ * (Gershgorin), omega_P = (4/3)/rho, and
+ *     P = (I - omega_P D_F^{-1} A_F) P_t.
+ * Entry order of evaluation (fixed so that it is reproducible):
+ *     s_ij = sum_{k in row i of A_F, ascending, agg(k) = j} aF_ik * t_k,
+ *     w_i  = omega_P / aF_ii,
+ *     P_ij = [j = agg(i)] * t_i - w_i * s_ij,
+ * with t_k = 1/sqrt(|agg(k)|).  The pattern is the structural union of the
+ * pattern of P_t and of A_F P_t; numerical zeros are kept.
+ */
+static int smoothed_prolongation(const ocsr *a, const double *diag, double eps,
+                                 const int32_t *agg, int64_t nagg, ocsr *P, double *omega_out) {
+    const int64_t n = a->nrows;
+    const double eps2 = eps * eps;
+    int64_t *cnt = (int64_t *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(int64_t));
+    double *tk = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *dF = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!cnt || !tk || !dF) { free(cnt); free(tk); free(dF); return O_OOM; }
+    for (int64_t i = 0; i < n; ++i) cnt[agg[i]]++;
+    for (int64_t i = 0; i < n; ++i) tk[i] = 1.0 / sqrt((double)cnt[agg[i]]);
+
+    /* filtered diagonal and Gershgorin estimate */
+    double rho = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double lump = 0.0;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j != i && !is_strong(a->val[k], diag[i], diag[j], eps2)) lump += a->val[k];
+        }
+        dF[i] = diag[i] - lump;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            if (j == i) s += fabs(dF[i]);
+            else if (is_strong(a->val[k], diag[i], diag[j], eps2)) s += fabs(a->val[k]);
+        }
+        double r = s / fabs(dF[i]);
+        if (r > rho) rho = r;
+    }
+    const double omega = (4.0 / 3.0) / rho;
+    *omega_out = omega;
+
+    /* row by row: dense accumulator over coarse columns */
+    double *acc = (double *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(double));
+    int64_t *mark = (int64_t *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int64_t));
+    int32_t *cols = (int32_t *)malloc((size_t)(nagg > 0 ? nagg : 1) * sizeof(int32_t));
+    /* first pass: count */
+    int64_t cap = 0;
+    for (int64_t i = 0; i < n; ++i) cap += a->ptr[i + 1] - a->ptr[i] + 1;
+    if (!acc || !mark || !cols || csr_alloc(P, n, nagg, cap) != O_OK) {
+        free(cnt); free(tk); free(dF); free(acc); free(mark); free(cols); return O_OOM;
+    }
+    for (int64_t c = 0; c < nagg; ++c) mark[c] = -1;
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t m = 0;
+        /* pattern: agg(i) and agg(k) for k in the row of A_F */
+        mark[agg[i]] = i; acc[agg[i]] = 0.0; cols[m++] = agg[i];
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) {
+            int64_t j = a->col[k];
+            int keep = (j == i) || is_strong(a->val[k], diag[i], diag[j], eps2);
+            if (!keep) continue;
+            int32_t c = agg[j];
+            if (mark[c] != i) { mark[c] = i; acc[c] = 0.0; cols[m++] = c; }
+            double afik = (j == i) ? dF[i] : a->val[k];
+            acc[c] += afik * tk[j];
+        }
+        qsort(cols, (size_t)m, sizeof(int32_t), cmp_i32);
+        const double w = omega / dF[i];
+        for (int64_t q = 0; q < m; ++q) {
+            int32_t c = cols[q];
+            double base = (c == agg[i]) ? tk[i] : 0.0;
+            P->col[pos] = c;
+            P->val[pos] = base - w * acc[c];
+            ++pos;
+        }
+        P->ptr[i + 1] = pos;
+    }
+    free(cnt); free(tk); free(dF); free(acc); free(mark); free(cols);
+    return O_OK;
+}
+
+/* R = P^T (Sec. 2: "a common choice for the restriction operator R is a
+ * transpose of the prolongation operator"); columns come out sorted because
+ * rows of P are visited in ascending order. */
+static int transpose(const ocsr *p, ocsr *r) {
+    const int64_t nnz = p->ptr[p->nrows];
+    if (csr_alloc(r, p->ncols, p->nrows, nnz) != O_OK) return O_OOM;
+    for (int64_t k = 0; k < nnz; ++k) r->ptr[p->col[k] + 1]++;
+    for (int64_t c = 0; c < p->ncols; ++c) r->ptr[c + 1] += r->ptr[c];
+    int64_t *fill = (int64_t *)malloc((size_t)(p->ncols > 0 ? p->ncols : 1) * sizeof(int64_t));
+    if (!fill) return O_OOM;
+    for (int64_t c = 0; c < p->ncols; ++c) fill[c] = r->ptr[c];
+    for (int64_t i = 0; i < p->nrows; ++i)
+        for (int64_t k = p->ptr[i]; k < p->ptr[i + 1]; ++k) {
+            int64_t dst = fill[p->col[k]]++;
+            r->col[dst] = (int32_t)i;
+            r->val[dst] = p->val[k];
+        }
+    free(fill);
+    return O_OK;
+}
+
+/* C = A B, row-wise (Gustavson).  Each entry is accumulated as
+ * ((0 + a_ik1 b_k1j) + a_ik2 b_k2j) + ... over the row of A in ascending k.
+ * The pattern is structural (products that happen to cancel are kept). */
+static int spgemm(const ocsr *a, const ocsr *b, ocsr *c) {
+    const int64_t n = a->nrows, m = b->ncols;
+    int64_t *mark = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    double *acc = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    int32_t *cols = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    if (!mark || !acc || !cols) { free(mark); free(acc); free(cols); return O_OOM; }
+    for (int64_t j = 0; j < m; ++j) mark[j] = -1;
+    /* symbolic */
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t ka = a->ptr[i]; ka < a->ptr[i + 1]; ++ka) {
+            int64_t k = a->col[ka];
+            for (int64_t kb = b->ptr[k]; kb < b->ptr[k + 1]; ++kb) {
+                int64_t j = b->col[kb];
+                if (mark[j] != i) { mark[j] = i; ++nnz; }
+            }
+        }
+    if (csr_alloc(c, n, m, nnz) != O_OK) { free(mark); free(acc); free(cols); return O_OOM; }
+    for (int64_t j = 0; j < m; ++j) mark[j] = -1;
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t cnt = 0;
+        for (int64_t ka = a->ptr[i]; ka < a->ptr[i + 1]; ++ka) {
+            int64_t k = a->col[ka];
+            double av = a->val[ka];
+            for (int64_t kb = b->ptr[k]; kb < b->ptr[k + 1]; ++kb) {
+                int64_t j = b->col[kb];
+                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols[cnt++] = (int32_t)j; }
+                acc[j] += av * b->val[kb];
+            }
+        }
+        qsort(cols, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        for (int64_t q = 0; q < cnt; ++q) { c->col[pos] = cols[q]; c->val[pos] = acc[cols[q]]; ++pos; }
+        c->ptr[i + 1] = pos;
+    }
+    free(mark); free(acc); free(cols);
+    return O_OK;
+}
+
+/* ------------------------------------------------- coarsest direct solver
+ * Algorithm 1, last step: "construct a direct solver for the coarsest
+ * system".  READING: dense LU with partial pivoting; the pivot is the entry of
+ * largest magnitude in the column, ties to the lowest row. */
+static int lu_factor(int64_t n, double *a, int64_t *piv) {
+    for (int64_t i = 0; i < n; ++i) piv[i] = i;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = k;
+        double best = fabs(a[k * n + k]);
+        for (int64_t i = k + 1; i < n; ++i)
+            if (fabs(a[i * n + k]) > best) { best = fabs(a[i * n + k]); p = i; }
+        if (best == 0.0) return O_INVALID; /* singular */
+        if (p != k) {
+            for (int64_t j = 0; j < n; ++j) { double t = a[k * n + j]; a[k * n + j] = a[p * n + j]; a[p * n + j] = t; }
+            int64_t t = piv[k]; piv[k] = piv[p]; piv[p] = t;
+        }
+        for (int64_t i = k + 1; i < n; ++i) {
+            double l = a[i * n + k] / a[k * n + k];
+            a[i * n + k] = l;
+            for (int64_t j = k + 1; j < n; ++j) a[i * n + j] -= l * a[k * n + j];
+        }
+    }
+    return O_OK;
+}
+
+static void lu_solve(int64_t n, const double *lu, const int64_t *piv, const double *b, double *x) {
+    for (int64_t i = 0; i < n; ++i) {
+        double s = b[piv[i]];
+        for (int64_t j = 0; j < i; ++j) s -= lu[i * n + j] * x[j];
+        x[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t j = i + 1; j < n; ++j) s -= lu[i * n + j] * x[j];
+        x[i] = s / lu[i * n + i];
+    }
+}
+
+/* ------------------------------------------------------ smoother diagonal
+ * Sec. 3 "Relaxation methods".  Damped Jacobi: d_i = omega / a_ii.
+ * READING for SPAI-0 (diagonal sparse approximate inverse, Broeker and Grote
+ * 2002): the diagonal M minimising ||I - M A||_F row by row,
+ * d_i = a_ii / sum_j a_ij^2 (row sum ascending). */
+static void smoother_diag(const ocsr *a, const double *diag, const oparams *prm, double *d) {
+    for (int64_t i = 0; i < a->nrows; ++i) {
+        if (prm->smoother == 1) {
+            double s = 0.0;
+            for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) s += a->val[k] * a->val[k];
+            d[i] = diag[i] / s;
+        } else {
+            d[i] = prm->jacobi_omega / diag[i];
+        }
+    }
+}
+
+/* ------------------------------------------------------------- setup
+ * Algorithm 1.  READING (stop rule): stop at n_l <= coarse_enough, at
+ * l + 1 = max_levels, or when aggregation stalls (n_{l+1} >= 0.95 n_l); a
+ * stall on a level larger than max_coarse_dense is an error, and so is a
+ * coarsest level larger than max_coarse_dense. */
+void orc_free(ohier *h);
+
+ohier *orc_setup(int64_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                 const oparams *prm, int *status) {
+    *status = O_OK;
+    if (n <= 0 || !ptr || !col || !val || !prm) { *status = O_INVALID; return NULL; }
+    ohier *h = (ohier *)calloc(1, sizeof(ohier));
+    if (!h) { *status = O_OOM; return NULL; }
+    /* copy level 0 */
+    olevel *L0 = &h->lev[0];
+    int64_t nnz = ptr[n];
+    if (csr_alloc(&L0->A, n, n, nnz) != O_OK) { *status = O_OOM; orc_free(h); return NULL; }
+    for (int64_t i = 0; i <= n; ++i) L0->A.ptr[i] = ptr[i];
+    memcpy(L0->A.col, col, (size_t)nnz * sizeof(int32_t));
+    memcpy(L0->A.val, val, (size_t)nnz * sizeof(double));
+    h->nlev = 1;
+
+    int l = 0;
+    for (;;) {
+        olevel *Lv = &h->lev[l];
+        const int64_t nl = Lv->A.nrows;
+        double *diag = (double *)malloc((size_t)nl * sizeof(double));
+        Lv->d = (double *)malloc((size_t)nl * sizeof(double));
+        Lv->f = (double *)calloc((size_t)nl, sizeof(double));
+        Lv->x = (double *)calloc((size_t)nl, sizeof(double));
+        Lv->t = (double *)calloc((size_t)nl, sizeof(double));
+        if (!diag || !Lv->d || !Lv->f || !Lv->x || !Lv->t) { free(diag); *status = O_OOM; break; }
+        for (int64_t i = 0; i < nl; ++i) diag[i] = diag_entry(&Lv->A, i);
+        for (int64_t i = 0; i < nl; ++i)
+            if (diag[i] == 0.0 || !isfinite(diag[i])) { *status = O_INVALID; break; }
+        if (*status != O_OK) { free(diag); break; }
+        smoother_diag(&Lv->A, diag, prm, Lv->d);
+
+        int coarsest = (nl <= prm->coarse_enough) || (l + 1 >= prm->max_levels) || (l + 1 >= OMAXLEV);
+        if (!coarsest) {
+            double eps = prm->eps_strong;
+            if (prm->eps_halving) for (int q = 0; q < l; ++q) eps *= 0.5;
+            Lv->agg = (int32_t *)malloc((size_t)nl * sizeof(int32_t));
+            if (!Lv->agg) { free(diag); *status = O_OOM; break; }
+            Lv->nagg = aggregate(&Lv->A, diag, eps, Lv->agg);
+            if (Lv->nagg < 0) { free(diag); *status = O_OOM; break; }
+            if ((double)Lv->nagg >= 0.95 * (double)nl) {
+                free(Lv->agg); Lv->agg = NULL; Lv->nagg = 0;
+                if (nl > prm->max_coarse_dense) { free(diag); *status = O_STALLED; break; }
+                coarsest = 1;
+            } else {
+                int st = smoothed_prolongation(&Lv->A, diag, eps, Lv->agg, Lv->nagg, &Lv->P, &Lv->omega_p);
+                if (st == O_OK) st = transpose(&Lv->P, &Lv->R);
+                ocsr AP = {0};
+                if (st == O_OK) st = spgemm(&Lv->A, &Lv->P, &AP);
+                if (st == O_OK) st = spgemm(&Lv->R, &AP, &h->lev[l + 1].A);
+                csr_free(&AP);
+                if (st != O_OK) { free(diag); *status = st; break; }
+                h->nlev = l + 2;
+            }
+        }
+        free(diag);
+        if (coarsest) {
+            if (nl > prm->max_coarse_dense) { *status = O_TOO_LARGE; break; }
+            h->nc = nl;
+            h->lu = (double *)calloc((size_t)(nl * nl), sizeof(double));
+            h->piv = (int64_t *)malloc((size_t)nl * sizeof(int64_t));
+            if (!h->lu || !h->piv) { *status = O_OOM; break; }
+            for (int64_t i = 0; i < nl; ++i)
+                for (int64_t k = Lv->A.ptr[i]; k < Lv->A.ptr[i + 1]; ++k)
+                    h->lu[i * nl + Lv->A.col[k]] = Lv->A.val[k];
+            if (lu_factor(nl, h->lu, h->piv) != O_OK) { *status = O_INVALID; break; }
+            break;
+        }
+        ++l;
+    }
+    if (*status == O_OK) {
+        h->work = (double *)calloc((size_t)(10 * n), sizeof(double));
+        if (!h->work) *status = O_OOM;
+    }
+    if (*status != O_OK) { orc_free(h); return NULL; }
+    return h;
+}
+
+void orc_free(ohier *h) {
+    if (!h) return;
+    for (int l = 0; l < OMAXLEV; ++l) {
+        olevel *Lv = &h->lev[l];
+        csr_free(&Lv->A); csr_free(&Lv->P); csr_free(&Lv->R);
+        free(Lv->agg); free(Lv->d); free(Lv->f); free(Lv->x); free(Lv->t);
+    }
+    free(h->lu); free(h->piv); free(h->work);
+    free(h);
+}
+
+/* ----------------------------------------------------------- V-cycle
+ * Algorithm 2, one pass of the loop body (the preconditioner, Sec. 2 last
+ * paragraph), applied to r with zero initial guess on every level:
+ *   for l = 0..L-2: x_l = 0; npre sweeps x_l <- x_l + d_l (f_l - A_l x_l)
+ *                   (the first sweep from zero is x_l = d_l f_l);
+ *                   f_{l+1} = R_l (f_l - A_l x_l)
+ *   x_{L-1} = A_{L-1}^{-1} f_{L-1}
+ *   for l = L-2..0: x_l += P_l x_{l+1}; npost sweeps.
+ */
+static void jacobi_sweep(const olevel *Lv, const double *f, double *x, double *tmp) {
+    const ocsr *a = &Lv->A;
+    for (int64_t i = 0; i < a->nrows; ++i) {
+        double s = 0.0;
+        for (int64_t k = a->ptr[i]; k < a->ptr[i + 1]; ++k) s += a->val[k] * x[a->col[k]];
+        tmp[i] = x[i] + Lv->d[i] * (f[i] - s);
+    }
+    memcpy(x, tmp, (size_t)a->nrows * sizeof(double));
+}
+
+void orc_vcycle(ohier *h, const double *r, double *z, const oparams *prm) {
+    const int L = h->nlev;
+    memcpy(h->lev[0].f, r, (size_t)h->lev[0].A.nrows * sizeof(double));
+    for (int l = 0; l < L - 1; ++l) {
+        olevel *Lv = &h->lev[l];
+        const int64_t n = Lv->A.nrows;
+        for (int64_t i = 0; i < n; ++i) Lv->x[i] = 0.0;
+        for (int s = 0; s < prm->npre; ++s) {
+            if (s == 0) for (int64_t i = 0; i < n; ++i) Lv->x[i] = Lv->d[i] * Lv->f[i];
+            else jacobi_sweep(Lv, Lv->f, Lv->x, Lv->t);
+        }
+        spmv(&Lv->A, Lv->x, Lv->t);
+        for (int64_t i = 0; i < n; ++i) Lv->t[i] = Lv->f[i] - Lv->t[i];
+        spmv(&Lv->R, Lv->t, h->lev[l + 1].f);
+    }
+    olevel *Lc = &h->lev[L - 1];
+    lu_solve(h->nc, h->lu, h->piv, Lc->f, Lc->x);
+    for (int l = L - 2; l >= 0; --l) {
+        olevel *Lv = &h->lev[l];
+        const int64_t n = Lv->A.nrows;
+        spmv(&Lv->P, h->lev[l + 1].x, Lv->t);
+        for (int64_t i = 0; i < n; ++i) Lv->x[i] += Lv->t[i];
+        for (int s = 0; s < prm->npost; ++s) jacobi_sweep(Lv, Lv->f, Lv->x, Lv->t);
+    }
+    memcpy(z, h->lev[0].x, (size_t)h->lev[0].A.nrows * sizeof(double));
+}
+
+/* ------------------------------------------------------------- Krylov
+ * CG (Sec. 3 "Iterative solvers"), preconditioned form of Saad, Iterative
+ * Methods for Sparse Linear Systems, Alg. 9.1.  READINGS: the stopping test
+ * is ||r|| / ||f|| <= rtol on the recurrence residual; the iteration count is
+ * the number of A p products in the loop; after the loop the true residual
+ * f - A x is formed and, if it misses rtol while iterations remain, the
+ * iteration restarts from it (p = z).  Breakdown: r.z or p.q not positive or
+ * not finite.  ||f|| = 0 gives x = 0 without iterating.
+ */
+int orc_cg(ohier *h, const double *f, double *x, double rtol, int maxiter, const oparams *prm,
+           int *iters_out, double *relres_out) {
+    const ocsr *A = &h->lev[0].A;
+    const int64_t n = A->nrows;
+    double *r = h->work, *z = r + n, *p = z + n, *q = p + n;
+    const double nf = sqrt(dot(n, f, f));
+    *iters_out = 0; *relres_out = 0.0;
+    if (nf == 0.0) { for (int64_t i = 0; i < n; ++i) x[i] = 0.0; return O_OK; }
+    int it = 0, status = O_OK;
+    for (;;) {
+        /* (re)start from the true residual */
+        spmv(A, x, r);
+        for (int64_t i = 0; i < n; ++i) r[i] = f[i] - r[i];
+        double res = sqrt(dot(n, r, r)) / nf;
+        *relres_out = res;
+        if (res <= rtol || it >= maxiter) break;
+        int first = 1;
+        double rho = 0.0;
+        while (res > rtol && it < maxiter) {
+            orc_vcycle(h, r, z, prm);
+            double rho_new = dot(n, r, z);
+            if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = O_BREAKDOWN; break; }
+            double beta = first ? 0.0 : rho_new / rho;
+            rho = rho_new; first = 0;
+            for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+            spmv(A, p, q);
+            double pq = dot(n, p, q);
+            if (!(pq > 0.0) || !isfinite(pq)) { status = O_BREAKDOWN; break; }
+            double alpha = rho / pq;
+            for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+            ++it;
+            res = sqrt(dot(n, r, r)) / nf;
+        }
+        if (status != O_OK) break;
+        /* true residual check happens at the top of the loop */
+    }
+    if (status == O_OK || status == O_BREAKDOWN) {
+        spmv(A, x, r);
+        for (int64_t i = 0; i < n; ++i) r[i] = f[i] - r[i];
+        *relres_out = sqrt(dot(n, r, r)) / nf;
+    }
+    *iters_out = it;
+    if (status == O_OK && *relres_out > rtol) status = O_NOT_CONVERGED;
+    return status;
+}
+
+/* BiCGStab (van der Vorst 1992), right-preconditioned, in the form of Saad
+ * Alg. 7.7 with M applied to p and s.  READINGS: shadow residual r^ = r_0;
+ * start rho_prev = alpha = omega = 1, v = p = 0; the half step that meets the
+ * tolerance on ||s|| ends the loop (x += alpha p^) and counts as an iteration;
+ * breakdown when rho, r^.v, t.t or omega is zero or not finite; same
+ * true-residual restart as CG. */
+int orc_bicgstab(ohier *h, const double *f, double *x, double rtol, int maxiter,
+                 const oparams *prm, int *iters_out, double *relres_out) {
+    const ocsr *A = &h->lev[0].A;
+    const int64_t n = A->nrows;
+    double *r = h->work, *rh = r + n, *p = rh + n, *v = p + n, *ph = v + n, *s = ph + n,
+           *sh = s + n, *t = sh + n;
+    const double nf = sqrt(dot(n, f, f));
+    *iters_out = 0; *relres_out = 0.0;
+    if (nf == 0.0) { for (int64_t i = 0; i < n; ++i) x[i] = 0.0; return O_OK; }
+    int it = 0, status = O_OK;
+    for (;;) {
+        spmv(A, x, r);
+        for (int64_t i = 0; i < n; ++i) r[i] = f[i] - r[i];
+        double res = sqrt(dot(n, r, r)) / nf;
+        *relres_out = res;
+        if (res <= rtol || it >= maxiter) break;
+        memcpy(rh, r, (size_t)n * sizeof(double));
+        for (int64_t i = 0; i < n; ++i) { p[i] = 0.0; v[i] = 0.0; }
+        double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+        while (res > rtol && it < maxiter) {
+            double rho = dot(n, rh, r);
+            if (rho == 0.0 || !isfinite(rho)) { status = O_BREAKDOWN; break; }
+            double beta = (rho / rho_prev) * (alpha / omega);
+            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            orc_vcycle(h, p, ph, prm);
+            spmv(A, ph, v);
+            double rv = dot(n, rh, v);
+            if (rv == 0.0 || !isfinite(rv)) { status = O_BREAKDOWN; break; }
+            alpha = rho / rv;
+            for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+            ++it;
+            double ress = sqrt(dot(n, s, s)) / nf;
+            if (ress <= rtol) {
+                for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
+                res = ress;
+                break;
+            }
+            orc_vcycle(h, s, sh, prm);
+            spmv(A, sh, t);
+            double tt = dot(n, t, t);
+            double ts = dot(n, t, s);
+            if (tt == 0.0 || !isfinite(tt)) { status = O_BREAKDOWN; break; }
+            omega = ts / tt;
+            if (omega == 0.0 || !isfinite(omega)) { status = O_BREAKDOWN; break; }
+            for (int64_t i = 0; i < n; ++i) {
+                x[i] += alpha * ph[i] + omega * sh[i];
+                r[i] = s[i] - omega * t[i];
+            }
+            rho_prev = rho;
+            res = sqrt(dot(n, r, r)) / nf;
+        }
+        if (status != O_OK) break;
+    }
+    spmv(A, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = f[i] - r[i];
+    *relres_out = sqrt(dot(n, r, r)) / nf;
+    *iters_out = it;
+    if (status == O_OK && *relres_out > rtol) status = O_NOT_CONVERGED;
+    return status;
+}
+
+/* ------------------------------------------------------- query / export */
+int orc_levels(const ohier *h) { return h->nlev; }
+
+/* out: n, nnz(A), ncoarse (aggregates), nnz(P), nnz(R) */
+void orc_level_info(const ohier *h, int l, int64_t *out) {
+    const olevel *Lv = &h->lev[l];
+    out[0] = Lv->A.nrows;
+    out[1] = Lv->A.ptr[Lv->A.nrows];
+    out[2] = (l < h->nlev - 1) ? Lv->nagg : 0;
+    out[3] = (l < h->nlev - 1) ? Lv->P.ptr[Lv->P.nrows] : 0;
+    out[4] = (l < h->nlev - 1) ? Lv->R.ptr[Lv->R.nrows] : 0;
+}
+
+static void export_csr(const ocsr *a, int64_t *ptr, int32_t *col, double *val) {
+    memcpy(ptr, a->ptr, (size_t)(a->nrows + 1) * sizeof(int64_t));
+    memcpy(col, a->col, (size_t)a->ptr[a->nrows] * sizeof(int32_t));
+    memcpy(val, a->val, (size_t)a->ptr[a->nrows] * sizeof(double));
+}
+
+/* which: 0 = A, 1 = P, 2 = R */
+void orc_get_matrix(const ohier *h, int l, int which, int64_t *ptr, int32_t *col, double *val) {
+    const olevel *Lv = &h->lev[l];
+    export_csr(which == 0 ? &Lv->A : which == 1 ? &Lv->P : &Lv->R, ptr, col, val);
+}
+
+void orc_get_level_vectors(const ohier *h, int l, int32_t *agg, double *d, double *omega_p) {
+    const olevel *Lv = &h->lev[l];
+    if (agg && Lv->agg) memcpy(agg, Lv->agg, (size_t)Lv->A.nrows * sizeof(int32_t));
+    if (d) memcpy(d, Lv->d, (size_t)Lv->A.nrows * sizeof(double));
+    if (omega_p) *omega_p = Lv->omega_p;
+}
+
+/* standalone steps, for the pins */
+static void wrap32(ocsr *a, int64_t n, int64_t m, const int32_t *ptr, const int32_t *col,
+                   const double *val) {
+    a->nrows = n; a->ncols = m;
+    a->ptr = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    for (int64_t i = 0; i <= n; ++i) a->ptr[i] = ptr[i];
+    a->col = (int32_t *)col; a->val = (double *)val;
+}
+
+int64_t orc_aggregate(int64_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                      double eps, int32_t *agg) {
+    ocsr a; wrap32(&a, n, n, ptr, col, val);
+    double *diag = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) diag[i] = diag_entry(&a, i);
+    int64_t r = aggregate(&a, diag, eps, agg);
+    free(diag); free(a.ptr);
+    return r;
+}
+
+void orc_strength(int64_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                  double eps, uint8_t *strong) {
+    ocsr a; wrap32(&a, n, n, ptr, col, val);
+    double *diag = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) diag[i] = diag_entry(&a, i);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = a.ptr[i]; k < a.ptr[i + 1]; ++k) {
+            int64_t j = col[k];
+            strong[k] = (uint8_t)(j != i && is_strong(val[k], diag[i], diag[j], eps * eps));
+        }
+    free(diag); free(a.ptr);
+}
+
+void orc_spmv(int64_t n, int64_t m, const int32_t *ptr, const int32_t *col, const double *val,
+              const double *x, double *y) {
+    ocsr a; wrap32(&a, n, m, ptr, col, val);
+    spmv(&a, x, y);
+    free(a.ptr);
+}
+
+/* C = A B on int32-indexed inputs; returns an opaque CSR to query and free */
+ocsr *orc_spgemm(int64_t n, int64_t k, int64_t m,
+                 const int32_t *pa, const int32_t *ca, const double *va,
+                 const int32_t *pb, const int32_t *cb, const double *vb) {
+    ocsr a, b;
+    wrap32(&a, n, k, pa, ca, va);
+    wrap32(&b, k, m, pb, cb, vb);
+    ocsr *c = (ocsr *)calloc(1, sizeof(ocsr));
+    int st = spgemm(&a, &b, c);
+    free(a.ptr); free(b.ptr);
+    if (st != O_OK) { csr_free(c); free(c); return NULL; }
+    return c;
+}
+
+int64_t orc_csr_nnz(const ocsr *c) { return c->ptr[c->nrows]; }
+void orc_csr_export(const ocsr *c, int64_t *ptr, int32_t *col, double *val) { export_csr(c, ptr, col, val); }
+void orc_csr_free(ocsr *c) { if (c) { csr_free(c); free(c); } }
+
+/* dense LU solve of a row-major n x n system (pins the coarsest solver) */
+int orc_dense_solve(int64_t n, const double *a, const double *b, double *x) {
+    double *lu = (double *)malloc((size_t)(n * n) * sizeof(double));
+    int64_t *piv = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    memcpy(lu, a, (size_t)(n * n) * sizeof(double));
+    int st = lu_factor(n, lu, piv);
+    if (st == O_OK) lu_solve(n, lu, piv, b, x);
+    free(lu); free(piv);
+    return st;
+}
+
+/* the smoothed prolongation of one level, standalone (agg from orc_aggregate) */
+ocsr *orc_prolongation(int64_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                       double eps, const int32_t *agg, int64_t nagg, double *omega_out) {
+    ocsr a; wrap32(&a, n, n, ptr, col, val);
+    double *diag = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) diag[i] = diag_entry(&a, i);
+    ocsr *p = (ocsr *)calloc(1, sizeof(ocsr));
+    int st = smoothed_prolongation(&a, diag, eps, agg, nagg, p, omega_out);
+    free(diag); free(a.ptr);
+    if (st != O_OK) { csr_free(p); free(p); return NULL; }
+    return p;
+}
+
+/* tentative prolongation values t_i = 1/sqrt(|agg(i)|) (S3), standalone */
+void orc_tentative_values(int64_t n, const int32_t *agg, int64_t nagg, double *t) {
+    int64_t *cnt = (int64_t *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) cnt[agg[i]]++;
+    for (int64_t i = 0; i < n; ++i) t[i] = 1.0 / sqrt((double)cnt[agg[i]]);
+    free(cnt);
+}
+
+void orc_smoother_diag(int64_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                       const oparams *prm, double *d) {
+    ocsr a; wrap32(&a, n, n, ptr, col, val);
+    double *diag = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) diag[i] = diag_entry(&a, i);
+    smoother_diag(&a, diag, prm, d);
+    free(diag); free(a.ptr);
+}
