@@ -1,0 +1,198 @@
+/*
+ * amg.h -- C ABI of the GB300 (sm_103a) smoothed-aggregation AMG solver.
+ *
+ * The library solves A x = f for a square sparse A with a Krylov method
+ * preconditioned by one AMG V-cycle per iteration:
+ *   - setup (Algorithm 1 of D. Demidov, "AMGCL: an Efficient, Flexible, and
+ *     Extensible Algebraic Multigrid Implementation"): while A_i is too big to
+ *     be solved directly, build the transfer operators P_i and R_i = P_i^T
+ *     (Sec. 2) by smoothed aggregation (Sec. 3, "Coarsening strategies") and
+ *     the Galerkin operator A_{i+1} = R_i A_i P_i; then a direct solver for
+ *     the coarsest A_L.  Aggregation and prolongation smoothing run on the
+ *     host; the Galerkin product runs on the GPU.
+ *   - solve (Algorithm 2, one V-cycle as the preconditioning step, Sec. 2 last
+ *     paragraph) inside CG or BiCGStab (Sec. 3, "Iterative solvers"), with
+ *     damped Jacobi or SPAI-0 smoothing (Sec. 3, "Relaxation methods").  The
+ *     whole iteration runs on the GPU; by default it is one CUDA-graph launch
+ *     whose loop is a device-side conditional node.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an amg_status; none aborts or exits.  On failure a
+ *     message is available from amg_last_error() (thread-local).
+ *   - Matrices are CSR: int32 row pointers (n + 1 entries, row_ptr[0] = 0),
+ *     int32 column indices sorted ascending within each row without
+ *     duplicates, float64 values.  nnz must be below 2^31.
+ *   - "device" pointers are CUDA device (or managed) memory of the device that
+ *     was current at amg_setup; "host" pointers are CPU memory.  Ownership of
+ *     every buffer passed in stays with the caller; the library copies what it
+ *     keeps.
+ *   - Work is issued on the CUDA stream given at amg_setup (NULL = legacy
+ *     default stream).  Calls that return results to the host synchronize
+ *     that stream.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_ERR_INVALID_ARG = 1,        /* bad pointer, size, CSR structure or zero diagonal */
+    AMG_ERR_OOM = 2,                /* device or host allocation failed */
+    AMG_ERR_CUDA = 3,               /* a CUDA runtime call failed */
+    AMG_ERR_NOT_CONVERGED = 4,      /* maxiter reached; x, iters, relres still valid */
+    AMG_ERR_BREAKDOWN = 5,          /* Krylov breakdown; x, iters, relres still valid */
+    AMG_ERR_COARSENING_STALLED = 6, /* aggregation stopped reducing a level too big to solve densely */
+    AMG_ERR_TOO_LARGE = 7           /* a size exceeds a documented limit */
+} amg_status;
+
+typedef enum { AMG_SMOOTHER_JACOBI = 0, AMG_SMOOTHER_SPAI0 = 1 } amg_smoother;
+typedef enum { AMG_SOLVER_CG = 0, AMG_SOLVER_BICGSTAB = 1 } amg_solver;
+/* FP64: hierarchy and V-cycle in float64.  FP32: the V-cycle (level
+ * matrices, smoother diagonals, level vectors) in float32 with float32
+ * accumulation, the outer Krylov vectors, dot products, the fine-level
+ * operator and the coarsest solve in float64. */
+typedef enum { AMG_PRECISION_FP64 = 0, AMG_PRECISION_FP32 = 1 } amg_precision;
+
+#define AMG_MAX_LEVELS 32
+
+/* Parameters (defaults from amg_params_default in brackets). */
+typedef struct {
+    double strength_eps;   /* [0.08] strength threshold on the finest level: j is a strong
+                              neighbour of i iff a_ij^2 > eps^2 |a_ii a_jj| */
+    int strength_halving;  /* [1] eps is halved on every coarser level */
+    int smoother;          /* [AMG_SMOOTHER_JACOBI] */
+    double jacobi_omega;   /* [0.72] damping of the Jacobi smoother */
+    int npre, npost;       /* [1, 1] smoothing sweeps before / after the coarse correction */
+    int coarse_enough;     /* [500] a level with at most this many rows is the coarsest */
+    int max_levels;        /* [25] at most this many levels (<= AMG_MAX_LEVELS) */
+    int max_coarse_dense;  /* [4096] largest coarsest level solved by a dense inverse */
+    int solver;            /* [AMG_SOLVER_CG] */
+    int precision;         /* [AMG_PRECISION_FP64] */
+    int use_graph;         /* [1] run the Krylov loop as one CUDA graph with a device-side
+                              while-node; 0 = host-driven launches (same kernels) */
+} amg_params;
+
+/* A CSR matrix as passed in by the caller (see the conventions above). */
+typedef struct {
+    int64_t n;               /* rows = columns */
+    int64_t nnz;             /* must equal row_ptr[n] */
+    const int32_t *row_ptr;  /* n + 1 */
+    const int32_t *col;      /* nnz */
+    const double *val;       /* nnz */
+    int on_device;           /* 0: the three arrays are host memory, 1: device memory */
+} amg_csr;
+
+typedef struct amg_handle amg_handle;
+
+/* Fill *p with the defaults listed above.  Error: INVALID_ARG if p is NULL. */
+amg_status amg_params_default(amg_params *p);
+
+/* Build the hierarchy of A (Algorithm 1) and keep it resident on the device.
+ * A is deep-copied; the caller may free it after the call.  prm may be NULL
+ * (defaults).  stream is a cudaStream_t (may be NULL) used by every later call
+ * on the handle.  Errors: INVALID_ARG (n < 1, broken CSR, zero or missing
+ * diagonal), COARSENING_STALLED, TOO_LARGE (coarsest level above
+ * max_coarse_dense, a Galerkin row wider than the GPU product supports),
+ * OOM, CUDA.  On error *out is NULL. */
+amg_status amg_setup(const amg_csr *A, const amg_params *prm, void *stream, amg_handle **out);
+
+/* Solve A x = f (Krylov method of the parameters, one V-cycle per
+ * preconditioner application).  f: device, n doubles.  x: device, n doubles,
+ * initial guess on entry, solution on return.  Stops when the relative
+ * recurrence residual ||r||/||f|| <= rtol or after maxiter iterations
+ * (iteration = one product with A inside the loop for CG; one pass of the
+ * loop body, including a final half step, for BiCGStab); then forms the true
+ * residual and, if it misses rtol while iterations remain, restarts from it.
+ * *iters (may be NULL): iterations done.  *relres (may be NULL): true relative
+ * residual ||f - A x||_2 / ||f||_2 in float64.  If ||f|| = 0: x = 0,
+ * iters = 0, relres = 0.  Returns NOT_CONVERGED or BREAKDOWN with valid x,
+ * iters and relres.  Synchronizes the handle's stream. */
+amg_status amg_solve(amg_handle *h, const double *f, double *x, double rtol, int maxiter,
+                     int *iters, double *relres);
+
+/* amg_solve with host buffers: f_host (n doubles) is copied to the device,
+ * x_host (n doubles) is the initial guess on entry and the solution on
+ * return.  The copies are part of the call (pinned host memory makes them
+ * faster).  Same results and errors as amg_solve. */
+amg_status amg_solve_host(amg_handle *h, const double *f_host, double *x_host, double rtol,
+                          int maxiter, int *iters, double *relres);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+amg_status amg_free(amg_handle *h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *amg_last_error(void);
+
+/* Hierarchy sizes.  levels: number of levels L.  rows, nnz_a: arrays of at
+ * least AMG_MAX_LEVELS entries, rows and nnz of A_l; nnz_p: nnz of P_l (0 on
+ * the coarsest level).  Any output may be NULL. */
+amg_status amg_hierarchy_info(const amg_handle *h, int *levels, int64_t *rows, int64_t *nnz_a,
+                              int64_t *nnz_p);
+
+/* Copy level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l) of level l to host
+ * arrays sized from amg_hierarchy_info: row_ptr (rows + 1), col and val (nnz).
+ * P and R do not exist on the coarsest level (INVALID_ARG). */
+amg_status amg_get_level_matrix(const amg_handle *h, int level, int which, int32_t *row_ptr,
+                                int32_t *col, double *val);
+
+/* Aggregate id of every row of level l (host array of rows[l] entries);
+ * INVALID_ARG on the coarsest level. */
+amg_status amg_get_aggregates(const amg_handle *h, int level, int32_t *agg);
+
+/* Smoother diagonal d_l of level l (host array of rows[l] doubles):
+ * Jacobi d_i = omega / a_ii, SPAI-0 d_i = a_ii / sum_j a_ij^2. */
+amg_status amg_get_smoother_diag(const amg_handle *h, int level, double *d);
+
+/* One V-cycle (Algorithm 2 body, zero initial guess on every level):
+ * z = M r.  r, z: device, n doubles, distinct buffers. */
+amg_status amg_apply_precond(amg_handle *h, const double *r, double *z);
+
+/* y = M x with the resident level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l)
+ * using the same SpMV kernel and schedule as the solve.  x: device, columns
+ * of that matrix; y: device, its rows. */
+amg_status amg_level_spmv(amg_handle *h, int level, int which, const double *x, double *y);
+
+/* Outer Krylov product of step (a1): y = A x and dot = x . y for a CSR matrix
+ * already on the device (A->on_device must be 1), on `stream`.  x, y: device,
+ * n doubles each, distinct.  dot: device, one double.  Scratch (the row-block
+ * schedule and per-block partial sums) is allocated with cudaMallocAsync on
+ * the stream and freed before returning.  The dot is summed in a fixed order
+ * (deterministic).  Errors: INVALID_ARG, OOM, CUDA. */
+amg_status amg_spmv_dot(const amg_csr *A, const double *x, double *y, double *dot, void *stream);
+
+/* Kernel classes reported by amg_solve_profile. */
+typedef enum {
+    AMG_KC_SPMV_DOT = 0,      /* q = A p with p.q (a1) */
+    AMG_KC_KRYLOV_UPDATE,     /* x, r updates with ||r||^2; p update (a2) */
+    AMG_KC_PRESMOOTH_L0,      /* finest level: x = d f, t = f - A x (a3 + a4 residual) */
+    AMG_KC_RESTRICT_L0,       /* finest level: f_1 = R t (a4 restriction) */
+    AMG_KC_PROLONG_L0,        /* finest level: x += P x_1 (a6) */
+    AMG_KC_POSTSMOOTH_L0,     /* finest level: z = x + d (f - A x) (a7) */
+    AMG_KC_VCYCLE_COARSER,    /* the same four kernels on levels >= 1 */
+    AMG_KC_COARSE_SOLVE,      /* dense coarsest solve (a5) */
+    AMG_KC_OTHER,             /* residual, norms and remaining small kernels */
+    AMG_KC_COUNT
+} amg_kernel_class;
+
+/* Same computation as amg_solve, but every kernel is launched from the host
+ * (no graph) between two CUDA events on the handle's stream; *ms receives
+ * the summed event time per kernel class (AMG_KC_COUNT doubles) and
+ * *launches the number of launches per class (AMG_KC_COUNT ints).  Used to
+ * attribute solve time to kernels; slower overall than amg_solve because of
+ * the per-launch events. */
+amg_status amg_solve_profile(amg_handle *h, const double *f, double *x, double rtol, int maxiter,
+                             int *iters, double *relres, double *ms, int *launches);
+
+/* Number of kernel launches the last amg_solve on this handle issued (all
+ * loop iterations included). */
+amg_status amg_last_launch_count(const amg_handle *h, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_GB300_H */

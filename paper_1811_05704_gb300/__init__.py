@@ -1,0 +1,278 @@
+"""Thin Python binding of the GB300 smoothed-aggregation AMG library.
+
+Every function here marshals arguments to the C ABI of include/amg.h (same
+names) and checks the returned status; all computation happens in the CUDA
+library libamg_gb300.so.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: importing this package fails if the compiled library is
+missing (build it with ``python paper_1811_05704_gb300/build.py`` or
+``__graft_entry__.build()``).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libamg_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"the CUDA library {LIB_PATH} is not built; run `python paper_1811_05704_gb300/build.py`")
+
+_lib = C.CDLL(LIB_PATH)
+
+# ----------------------------------------------------------------- constants
+AMG_OK, AMG_ERR_INVALID_ARG, AMG_ERR_OOM, AMG_ERR_CUDA = 0, 1, 2, 3
+AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_COARSENING_STALLED, AMG_ERR_TOO_LARGE = 4, 5, 6, 7
+AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SPAI0 = 0, 1
+AMG_SOLVER_CG, AMG_SOLVER_BICGSTAB = 0, 1
+AMG_PRECISION_FP64, AMG_PRECISION_FP32 = 0, 1
+AMG_MAX_LEVELS = 32
+KERNEL_CLASSES = ["spmv_dot", "krylov_update", "presmooth_l0", "restrict_l0", "prolong_l0",
+                  "postsmooth_l0", "vcycle_coarser", "coarse_solve", "other"]
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED",
+                5: "BREAKDOWN", 6: "COARSENING_STALLED", 7: "TOO_LARGE"}
+
+
+class amg_params(C.Structure):
+    _fields_ = [
+        ("strength_eps", C.c_double),
+        ("strength_halving", C.c_int),
+        ("smoother", C.c_int),
+        ("jacobi_omega", C.c_double),
+        ("npre", C.c_int),
+        ("npost", C.c_int),
+        ("coarse_enough", C.c_int),
+        ("max_levels", C.c_int),
+        ("max_coarse_dense", C.c_int),
+        ("solver", C.c_int),
+        ("precision", C.c_int),
+        ("use_graph", C.c_int),
+    ]
+
+
+class amg_csr(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("nnz", C.c_int64),
+        ("row_ptr", C.c_void_p),
+        ("col", C.c_void_p),
+        ("val", C.c_void_p),
+        ("on_device", C.c_int),
+    ]
+
+
+_VP, _I, _D, _I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+_sigs = {
+    "amg_params_default": [C.POINTER(amg_params)],
+    "amg_setup": [C.POINTER(amg_csr), C.POINTER(amg_params), _VP, C.POINTER(_VP)],
+    "amg_solve": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D)],
+    "amg_solve_host": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D)],
+    "amg_free": [_VP],
+    "amg_hierarchy_info": [_VP, C.POINTER(_I), _VP, _VP, _VP],
+    "amg_get_level_matrix": [_VP, _I, _I, _VP, _VP, _VP],
+    "amg_get_aggregates": [_VP, _I, _VP],
+    "amg_get_smoother_diag": [_VP, _I, _VP],
+    "amg_apply_precond": [_VP, _VP, _VP],
+    "amg_level_spmv": [_VP, _I, _I, _VP, _VP],
+    "amg_spmv_dot": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
+    "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
+    "amg_last_launch_count": [_VP, C.POINTER(_I64)],
+}
+for _name, _args in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.amg_last_error.restype = C.c_char_p
+_lib.amg_last_error.argtypes = []
+
+EXPORTED = sorted(list(_sigs) + ["amg_last_error"])
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.amg_last_error().decode()
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, where, allow=()):
+    if st != AMG_OK and st not in allow:
+        raise AmgError(st, where)
+    return st
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor or numpy array (contiguous)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------ C-ABI names
+def amg_last_error() -> str:
+    return _lib.amg_last_error().decode()
+
+
+def amg_params_default(**overrides) -> amg_params:
+    p = amg_params()
+    _check(_lib.amg_params_default(C.byref(p)), "amg_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_csr(n, row_ptr, col, val):
+    """amg_csr over host numpy arrays (int32, int32, float64) or CUDA tensors."""
+    on_device = not isinstance(val, np.ndarray)
+    return amg_csr(n=n, nnz=int(len(col) if isinstance(col, np.ndarray) else col.numel()),
+                   row_ptr=_ptr(row_ptr), col=_ptr(col), val=_ptr(val), on_device=int(on_device))
+
+
+def amg_setup(csr: amg_csr, params: amg_params = None, stream=None):
+    h = C.c_void_p()
+    p = C.byref(params) if params is not None else None
+    _check(_lib.amg_setup(C.byref(csr), p, _stream(stream), C.byref(h)), "amg_setup")
+    return h
+
+
+def amg_free(h):
+    _check(_lib.amg_free(h), "amg_free")
+
+
+def amg_solve(h, f, x, rtol=1e-8, maxiter=500, raise_on=()):
+    """Solve on device tensors f, x (x: initial guess in, solution out).
+
+    Returns (status, iterations, true relative residual).  NOT_CONVERGED and
+    BREAKDOWN are returned, not raised, unless listed in raise_on."""
+    it, rr = C.c_int(), C.c_double()
+    st = _lib.amg_solve(h, _ptr(f), _ptr(x), rtol, maxiter, C.byref(it), C.byref(rr))
+    allow = tuple(s for s in (AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN) if s not in raise_on)
+    _check(st, "amg_solve", allow)
+    return st, it.value, rr.value
+
+
+def amg_solve_host(h, f_host, x_host, rtol=1e-8, maxiter=500):
+    it, rr = C.c_int(), C.c_double()
+    st = _lib.amg_solve_host(h, _ptr(f_host), _ptr(x_host), rtol, maxiter, C.byref(it), C.byref(rr))
+    _check(st, "amg_solve_host", (AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN))
+    return st, it.value, rr.value
+
+
+def amg_solve_profile(h, f, x, rtol=1e-8, maxiter=500):
+    """Returns (status, iterations, relres, {class: ms}, {class: launches})."""
+    it, rr = C.c_int(), C.c_double()
+    ms = (C.c_double * len(KERNEL_CLASSES))()
+    ln = (C.c_int * len(KERNEL_CLASSES))()
+    st = _lib.amg_solve_profile(h, _ptr(f), _ptr(x), rtol, maxiter, C.byref(it), C.byref(rr),
+                                C.cast(ms, C.c_void_p), C.cast(ln, C.c_void_p))
+    _check(st, "amg_solve_profile", (AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN))
+    return (st, it.value, rr.value, dict(zip(KERNEL_CLASSES, list(ms))),
+            dict(zip(KERNEL_CLASSES, list(ln))))
+
+
+def amg_last_launch_count(h) -> int:
+    v = C.c_int64()
+    _check(_lib.amg_last_launch_count(h, C.byref(v)), "amg_last_launch_count")
+    return v.value
+
+
+def amg_hierarchy_info(h):
+    lv = C.c_int()
+    rows = np.zeros(AMG_MAX_LEVELS, np.int64)
+    nnz = np.zeros(AMG_MAX_LEVELS, np.int64)
+    nnzp = np.zeros(AMG_MAX_LEVELS, np.int64)
+    _check(_lib.amg_hierarchy_info(h, C.byref(lv), rows.ctypes.data, nnz.ctypes.data,
+                                   nnzp.ctypes.data), "amg_hierarchy_info")
+    L = lv.value
+    return dict(levels=L, rows=rows[:L].tolist(), nnz=nnz[:L].tolist(), nnz_p=nnzp[:L].tolist())
+
+
+def amg_get_level_matrix(h, level, which):
+    """which in {'A','P','R'} -> (row_ptr int32, col int32, val float64, shape)."""
+    info = amg_hierarchy_info(h)
+    w = {"A": 0, "P": 1, "R": 2}[which]
+    n = info["rows"][level]
+    nc = info["rows"][level + 1] if level + 1 < info["levels"] else 0
+    nrows = nc if which == "R" else n
+    ncols = nc if which == "P" else n
+    nnz = info["nnz"][level] if which == "A" else info["nnz_p"][level]
+    ptr = np.zeros(nrows + 1, np.int32)
+    col = np.zeros(max(nnz, 1), np.int32)
+    val = np.zeros(max(nnz, 1), np.float64)
+    _check(_lib.amg_get_level_matrix(h, level, w, ptr.ctypes.data, col.ctypes.data, val.ctypes.data),
+           "amg_get_level_matrix")
+    return ptr, col[:nnz], val[:nnz], (nrows, ncols)
+
+
+def amg_get_aggregates(h, level):
+    n = amg_hierarchy_info(h)["rows"][level]
+    agg = np.zeros(n, np.int32)
+    _check(_lib.amg_get_aggregates(h, level, agg.ctypes.data), "amg_get_aggregates")
+    return agg
+
+
+def amg_get_smoother_diag(h, level):
+    n = amg_hierarchy_info(h)["rows"][level]
+    d = np.zeros(n, np.float64)
+    _check(_lib.amg_get_smoother_diag(h, level, d.ctypes.data), "amg_get_smoother_diag")
+    return d
+
+
+def amg_apply_precond(h, r, z):
+    _check(_lib.amg_apply_precond(h, _ptr(r), _ptr(z)), "amg_apply_precond")
+
+
+def amg_level_spmv(h, level, which, x, y):
+    w = {"A": 0, "P": 1, "R": 2}[which]
+    _check(_lib.amg_level_spmv(h, level, w, _ptr(x), _ptr(y)), "amg_level_spmv")
+
+
+def amg_spmv_dot(csr: amg_csr, x, y, dot, stream=None):
+    _check(_lib.amg_spmv_dot(C.byref(csr), _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
+           "amg_spmv_dot")
+
+
+# ------------------------------------------------------------- convenience
+class Solver:
+    """Owns a handle: Solver(n, row_ptr, col, val, **params).solve(f, x)."""
+
+    def __init__(self, n, row_ptr, col, val, stream=None, **params):
+        self._keep = (row_ptr, col, val)
+        self.params = amg_params_default(**params)
+        self.handle = amg_setup(make_csr(n, row_ptr, col, val), self.params, stream)
+        self.n = n
+
+    def close(self):
+        if getattr(self, "handle", None):
+            amg_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, f, x, rtol=1e-8, maxiter=500):
+        return amg_solve(self.handle, f, x, rtol, maxiter)
+
+    def info(self):
+        return amg_hierarchy_info(self.handle)

@@ -1,0 +1,193 @@
+// amg_internal.h -- declarations shared by the library's translation units.
+// Not part of the public ABI (include/amg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+// ----------------------------------------------------------------- errors
+struct Error {
+    amg_status status;
+    std::string msg;
+};
+// Throwing is internal only; every extern "C" entry point catches and turns
+// the exception into a status + thread-local message.
+[[noreturn]] void fail(amg_status st, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define AMG_CUDA(call) ::amg::cuda_check((call), #call)
+
+// ------------------------------------------------------------ host CSR
+struct HostCsr {
+    int64_t nrows = 0, ncols = 0;
+    std::vector<int32_t> ptr;  // nrows + 1
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// Host part of the setup (setup_host.cpp).  Each function implements one
+// step of smoothed aggregation; see the comments there for the readings.
+std::vector<double> host_diagonal(const HostCsr& A);  // fails on a zero / missing diagonal
+void host_validate(const HostCsr& A);                  // CSR structure checks
+int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double eps,
+                       std::vector<int32_t>& agg);
+void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double eps,
+                       const std::vector<int32_t>& agg, int64_t nagg, HostCsr& P,
+                       double& omega);
+void host_transpose(const HostCsr& P, HostCsr& R);
+void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const amg_params& prm,
+                        std::vector<double>& d);
+void host_dense_inverse(const HostCsr& A, std::vector<double>& inv);  // row-major n x n
+std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_cap, int nnz_cap);
+
+// ---------------------------------------------------------- device CSR
+// Row-block schedule: block b of the SpMV kernel covers rows
+// [blk[b], blk[b+1]); at most kRowsPerBlock rows and (unless a single row)
+// at most kTileNnz nonzeros, so one block's products fit one shared tile.
+constexpr int kThreads = 256;
+constexpr int kRowsPerBlock = 256;
+constexpr int kTileNnz = 2048;
+
+struct DevCsr {
+    int32_t nrows = 0, ncols = 0;
+    int64_t nnz = 0;
+    int32_t* ptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    float* val32 = nullptr;  // float32 copy (mixed-precision V-cycle), optional
+    int32_t* blk = nullptr;  // row-block schedule
+    int32_t nblk = 0;
+};
+
+// ------------------------------------------------------- Krylov state
+// Lives in device memory; scalars of the Krylov recurrences are computed on
+// the device by the last block of the kernel that produced the dot products.
+struct KState {
+    double rtol;
+    int maxiter;
+    int it;
+    int status;      // 0 ok, AMG_ERR_BREAKDOWN
+    int halt;        // stop everything (breakdown, or nothing to do)
+    int skip2;       // BiCGStab: skip the second half of the step
+    int half;        // BiCGStab: converged at the half step
+    int first;       // CG: next beta is 0
+    int cond;        // last loop condition value
+    int zero_rhs;    // ||f|| == 0
+    double nf;       // ||f||
+    double res;      // recurrence residual / ||f||
+    double relres;   // true residual / ||f|| (after the loop)
+    double rho, rho_prev, alpha, omega, beta;
+    double dots[4];
+};
+
+// What the last block of a dot-producing kernel does with the sums.
+enum Fin : int {
+    FIN_NONE = 0,    // store dots into st->dots
+    FIN_INIT,        // dots: (r.r, f.f): nf, res, loop condition
+    FIN_CG_RHO,      // dot: r.z -> beta, rho
+    FIN_CG_ALPHA,    // dot: p.q -> alpha
+    FIN_CG_RES,      // dot: r.r -> it++, res, loop condition
+    FIN_TRUE,        // dot: r.r of the true residual -> relres
+    FIN_BI_INIT,     // dots: (r.r, f.f): as FIN_INIT plus rho = r.r, beta
+    FIN_BI_ALPHA,    // dot: rh.v -> alpha
+    FIN_BI_HALF,     // dot: s.s -> it++, half-step test
+    FIN_BI_OMEGA,    // dots: (t.t, t.s) -> omega
+    FIN_BI_RES,      // dots: (r.r, rh.r) -> rho, beta, res, loop condition
+};
+
+struct Reduce {
+    double* partial = nullptr;      // two arrays of `stride` per-block sums
+    int stride = 0;                 // >= grid size of any kernel using this buffer
+    unsigned int* counter = nullptr;
+    KState* st = nullptr;
+    int fin = FIN_NONE;
+    int set_cond = 0;               // call cudaGraphSetConditional (graph launches only)
+    unsigned long long cond_handle = 0;
+    double* out = nullptr;          // FIN_NONE with out != nullptr: write dot[0] there
+};
+constexpr int kMaxReduceBlocks = 1 << 22;  // sanity cap on a reducing grid
+
+// ------------------------------------------------------------ launchers
+// SpMV-engine kernels (spmv.cu).  `skip` (may be null): if *skip != 0 the
+// kernel returns at once (device-side early exit inside graph loops).
+// y = A x
+void launch_spmv(const DevCsr& A, const double* x, double* y, const int* skip, cudaStream_t s);
+// y = A x and dot(w, y) reduced through r (w = x if null)
+void launch_spmv_dot(const DevCsr& A, const double* x, const double* w, double* y,
+                     const Reduce& r, const int* skip, cudaStream_t s);
+// y = A x and dots (y.y, y.w)
+void launch_spmv_dot2(const DevCsr& A, const double* x, const double* w, double* y,
+                      const Reduce& r, const int* skip, cudaStream_t s);
+// t = f - A x (no dots)
+void launch_residual_plain(const DevCsr& A, const double* f, const double* x, double* t,
+                           const int* skip, cudaStream_t s);
+// x = d f (elementwise)
+void launch_scale(const double* d, const double* f, double* x, int64_t n, const int* skip,
+                  cudaStream_t s);
+int vec_grid(int64_t n);
+// standalone, uniform rows-per-block schedule, bounds-checked columns
+void launch_spmv_dot_uniform(int32_t n, int32_t ncols, const int32_t* ptr, const int32_t* col,
+                             const double* val, const double* x, double* y, int rows_per_block,
+                             const Reduce& r, int* err_flag, cudaStream_t s);
+// x = d f, t = f - A x
+void launch_presmooth_residual(const DevCsr& A, const double* d, const double* f, double* x,
+                               double* t, const int* skip, cudaStream_t s);
+// y = x + d (f - A x), optional dot(w, y)
+void launch_smooth(const DevCsr& A, const double* d, const double* f, const double* x, double* y,
+                   const double* w, const Reduce* r, const int* skip, cudaStream_t s);
+// r = f - A x with dots (r.r, f.f); optional copy of r to r2
+void launch_residual(const DevCsr& A, const double* f, const double* x, double* r, double* r2,
+                     const Reduce& red, const int* skip, cudaStream_t s);
+// x += P xc
+void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int* skip,
+                        cudaStream_t s);
+
+// float32 V-cycle variants (mixed precision)
+void launch_spmv_f32(const DevCsr& A, const float* x, float* y, const int* skip, cudaStream_t s);
+void launch_presmooth_residual_f32(const DevCsr& A, const float* d, const float* f32,
+                                   const double* f64, float* x, float* t, const int* skip,
+                                   cudaStream_t s);
+void launch_smooth_f32(const DevCsr& A, const float* d, const float* f32, const double* f64,
+                       const float* x, float* y32, double* y64, const double* w,
+                       const Reduce* r, const int* skip, cudaStream_t s);
+void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const int* skip,
+                            cudaStream_t s);
+
+// vector kernels
+void launch_fill(double* x, double v, int64_t n, cudaStream_t s);
+void launch_cg_pupdate(KState* st, const double* z, double* p, int64_t n, cudaStream_t s);
+void launch_cg_update(const Reduce& r, const double* p, const double* q, double* x, double* rv,
+                      int64_t n, cudaStream_t s);
+void launch_bi_pupdate(KState* st, const double* r, const double* v, double* p, int64_t n,
+                       cudaStream_t s);
+void launch_bi_s(const Reduce& red, const double* r, const double* v, double* sv, int64_t n,
+                 cudaStream_t s);
+void launch_bi_update(const Reduce& red, const double* rh, const double* ph, const double* sh,
+                      const double* sv, const double* t, double* x, double* rv, int64_t n,
+                      cudaStream_t s);
+void launch_dot2(const Reduce& red, const double* a, const double* b, const double* c,
+                 const double* d, int64_t n, const int* skip, cudaStream_t s);
+void launch_coarse_solve(const double* inv, int32_t n, const double* f, double* x,
+                         const int* skip, cudaStream_t s);
+void launch_coarse_solve_f32(const double* inv, int32_t n, const float* f, float* x,
+                             const int* skip, cudaStream_t s);
+void launch_copy_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_validate_csr(int32_t n, int64_t nnz, const int32_t* ptr, int* err, cudaStream_t s);
+
+// Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
+// entries accumulated in ascending order of the inner index.
+void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s);
+
+// device memory helpers
+template <typename T>
+T* dev_alloc(size_t count);
+void dev_free(void* p);
+
+}  // namespace amg

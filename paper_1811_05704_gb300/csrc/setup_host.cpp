@@ -1,0 +1,295 @@
+// setup_host.cpp -- host part of the smoothed-aggregation setup.
+//
+// The paper builds the whole hierarchy on the CPU (Sec. 3, design principles:
+// the setup is "intrinsically serial", the hierarchy is then moved into the
+// backend).  This library keeps the serial graph work here -- strength of
+// connection, aggregation, the smoothed prolongation and R = P^T -- and runs
+// the Galerkin product R A P on the GPU (spgemm.cu).
+//
+// Floating-point decisions (strength test, pass-2 argmax) and the prolongation
+// values are evaluated in a fixed order with no FMA contraction (the file is
+// built with -ffp-contract=off), so that the aggregates and P are reproducible
+// bit for bit from the level matrix.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+void host_validate(const HostCsr& A) {
+    if (A.nrows < 1) fail(AMG_ERR_INVALID_ARG, "matrix has no rows");
+    if ((int64_t)A.ptr.size() != A.nrows + 1) fail(AMG_ERR_INVALID_ARG, "row_ptr size");
+    if (A.ptr[0] != 0) fail(AMG_ERR_INVALID_ARG, "row_ptr[0] != 0");
+    for (int64_t i = 0; i < A.nrows; ++i) {
+        if (A.ptr[i + 1] < A.ptr[i]) fail(AMG_ERR_INVALID_ARG, "row_ptr not monotone at row " + std::to_string(i));
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            if (A.col[k] < 0 || A.col[k] >= A.ncols)
+                fail(AMG_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
+            if (k > A.ptr[i] && A.col[k] <= A.col[k - 1])
+                fail(AMG_ERR_INVALID_ARG, "columns not strictly ascending in row " + std::to_string(i));
+            if (!std::isfinite(A.val[k]))
+                fail(AMG_ERR_INVALID_ARG, "non-finite value in row " + std::to_string(i));
+        }
+    }
+}
+
+std::vector<double> host_diagonal(const HostCsr& A) {
+    std::vector<double> dg(A.nrows, 0.0);
+    for (int64_t i = 0; i < A.nrows; ++i) {
+        const int32_t* b = A.col.data() + A.ptr[i];
+        const int32_t* e = A.col.data() + A.ptr[i + 1];
+        const int32_t* it = std::lower_bound(b, e, (int32_t)i);
+        if (it != e && *it == i) dg[i] = A.val[it - A.col.data()];
+        if (dg[i] == 0.0)
+            fail(AMG_ERR_INVALID_ARG, "zero or missing diagonal in row " + std::to_string(i));
+    }
+    return dg;
+}
+
+namespace {
+
+// Strength of connection (Vanek, Mandel and Brezina 1996, the smoothed
+// aggregation the paper cites in Sec. 3): j != i is strong for i iff
+// a_ij^2 > eps^2 |a_ii a_jj|, decided from row i.
+std::vector<uint8_t> strong_mask(const HostCsr& A, const std::vector<double>& dg, double eps) {
+    const double e2 = eps * eps;
+    std::vector<uint8_t> s(A.nnz(), 0);
+    for (int64_t i = 0; i < A.nrows; ++i)
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            const int32_t j = A.col[k];
+            const double a = A.val[k];
+            s[k] = (j != i) && (a * a > e2 * std::fabs(dg[i] * dg[j]));
+        }
+    return s;
+}
+
+}  // namespace
+
+// Plain aggregation in four passes: (0) nodes without strong neighbours are
+// singletons; (1) in row order, a free node whose strong neighbours are all
+// free seeds an aggregate with them; (2) every node still free joins, as
+// assigned after pass 1, the aggregate of its strong neighbour with the
+// largest |a_ij| / sqrt(|a_ii a_jj|), the lowest j on ties; (3) any node still
+// free seeds an aggregate with its free strong neighbours.  Ids are given in
+// creation order.
+int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double eps,
+                       std::vector<int32_t>& agg) {
+    const int64_t n = A.nrows;
+    const std::vector<uint8_t> s = strong_mask(A, dg, eps);
+    agg.assign(n, -1);
+    int32_t next = 0;
+
+    std::vector<int32_t> degree(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) degree[i] += s[k];
+
+    for (int64_t i = 0; i < n; ++i)
+        if (degree[i] == 0) agg[i] = next++;
+
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] != -1) continue;
+        bool free_nbhd = true;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (s[k] && agg[A.col[k]] != -1) { free_nbhd = false; break; }
+        if (!free_nbhd) continue;
+        agg[i] = next;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (s[k]) agg[A.col[k]] = next;
+        ++next;
+    }
+
+    const std::vector<int32_t> after1(agg);
+    for (int64_t i = 0; i < n; ++i) {
+        if (after1[i] != -1) continue;
+        int32_t pick = -1;
+        double best = -1.0;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            if (!s[k]) continue;
+            const int32_t j = A.col[k];
+            if (after1[j] == -1) continue;
+            const double c = std::fabs(A.val[k]) / std::sqrt(std::fabs(dg[i] * dg[j]));
+            if (c > best) { best = c; pick = after1[j]; }
+        }
+        if (pick != -1) agg[i] = pick;
+    }
+
+    for (int64_t i = 0; i < n; ++i) {
+        if (agg[i] != -1) continue;
+        agg[i] = next;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (s[k] && agg[A.col[k]] == -1) agg[A.col[k]] = next;
+        ++next;
+    }
+    return next;
+}
+
+// Smoothed prolongation P = (I - omega D_F^{-1} A_F) P_t.
+//   P_t(i, agg(i)) = t_i = 1/sqrt(|agg(i)|).
+//   A_F: diagonal and strong entries; weak entries of a row are summed in
+//   column order and subtracted from the diagonal (aF_ii = a_ii - sum_weak).
+//   omega = (4/3) / rho, rho = max_i (sum over the row of A_F, in column
+//   order, of |aF_ij|) / |aF_ii|.
+//   P_ij = [j == agg(i)] t_i - (omega / aF_ii) * s_ij, where s_ij sums
+//   aF_ik t_k over the row of A_F in column order for the k with agg(k) = j.
+// The pattern of row i is {agg(i)} union {agg(k): k in the row of A_F},
+// sorted; entries that evaluate to zero are kept.
+void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double eps,
+                       const std::vector<int32_t>& agg, int64_t nagg, HostCsr& P,
+                       double& omega) {
+    const int64_t n = A.nrows;
+    const std::vector<uint8_t> s = strong_mask(A, dg, eps);
+
+    std::vector<int64_t> size(nagg, 0);
+    for (int64_t i = 0; i < n; ++i) size[agg[i]]++;
+    std::vector<double> t(n);
+    for (int64_t i = 0; i < n; ++i) t[i] = 1.0 / std::sqrt((double)size[agg[i]]);
+
+    std::vector<double> dF(n);
+    for (int64_t i = 0; i < n; ++i) {
+        double weak = 0.0;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (A.col[k] != i && !s[k]) weak += A.val[k];
+        dF[i] = dg[i] - weak;
+    }
+    double rho = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double row = 0.0;
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            if (A.col[k] == i) row += std::fabs(dF[i]);
+            else if (s[k]) row += std::fabs(A.val[k]);
+        }
+        rho = std::max(rho, row / std::fabs(dF[i]));
+    }
+    omega = (4.0 / 3.0) / rho;
+
+    P.nrows = n;
+    P.ncols = nagg;
+    P.ptr.assign(n + 1, 0);
+    P.col.clear();
+    P.val.clear();
+    P.col.reserve(A.nnz() + n);
+    P.val.reserve(A.nnz() + n);
+    std::vector<std::pair<int32_t, double>> row;  // (coarse column, s_ij), few entries
+    for (int64_t i = 0; i < n; ++i) {
+        row.clear();
+        row.emplace_back(agg[i], 0.0);
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            const int32_t j = A.col[k];
+            if (j != i && !s[k]) continue;
+            const double a = (j == i) ? dF[i] : A.val[k];
+            const int32_t c = agg[j];
+            auto it = std::find_if(row.begin(), row.end(),
+                                   [c](const std::pair<int32_t, double>& e) { return e.first == c; });
+            if (it == row.end()) it = row.emplace(row.end(), c, 0.0);
+            it->second += a * t[j];
+        }
+        std::sort(row.begin(), row.end());
+        const double w = omega / dF[i];
+        for (const auto& e : row) {
+            const double base = (e.first == agg[i]) ? t[i] : 0.0;
+            P.col.push_back(e.first);
+            P.val.push_back(base - w * e.second);
+        }
+        P.ptr[i + 1] = (int32_t)P.col.size();
+    }
+}
+
+// R = P^T (Sec. 2), columns ascending.
+void host_transpose(const HostCsr& P, HostCsr& R) {
+    R.nrows = P.ncols;
+    R.ncols = P.nrows;
+    R.ptr.assign(R.nrows + 1, 0);
+    R.col.resize(P.nnz());
+    R.val.resize(P.nnz());
+    for (int64_t k = 0; k < P.nnz(); ++k) R.ptr[P.col[k] + 1]++;
+    for (int64_t c = 0; c < R.nrows; ++c) R.ptr[c + 1] += R.ptr[c];
+    std::vector<int32_t> pos(R.ptr.begin(), R.ptr.end() - 1);
+    for (int64_t i = 0; i < P.nrows; ++i)
+        for (int32_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+            const int32_t dst = pos[P.col[k]]++;
+            R.col[dst] = (int32_t)i;
+            R.val[dst] = P.val[k];
+        }
+}
+
+// Smoother diagonal (Sec. 3, relaxation): damped Jacobi omega / a_ii, or
+// SPAI-0, the diagonal minimising ||I - D A||_F: a_ii / sum_j a_ij^2.
+void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const amg_params& prm,
+                        std::vector<double>& d) {
+    d.resize(A.nrows);
+    for (int64_t i = 0; i < A.nrows; ++i) {
+        if (prm.smoother == AMG_SMOOTHER_SPAI0) {
+            double s2 = 0.0;
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s2 += A.val[k] * A.val[k];
+            d[i] = dg[i] / s2;
+        } else {
+            d[i] = prm.jacobi_omega / dg[i];
+        }
+    }
+}
+
+// Coarsest direct solver (Algorithm 1, last step): LU with partial pivoting
+// (largest magnitude, lowest row on ties), then the explicit inverse, so that
+// the solve on the GPU is one matrix-vector product.
+void host_dense_inverse(const HostCsr& A, std::vector<double>& inv) {
+    const int64_t n = A.nrows;
+    std::vector<double> a(n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) a[i * n + A.col[k]] = A.val[k];
+    std::vector<int64_t> perm(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t p = c;
+        for (int64_t i = c + 1; i < n; ++i)
+            if (std::fabs(a[i * n + c]) > std::fabs(a[p * n + c])) p = i;
+        if (a[p * n + c] == 0.0) fail(AMG_ERR_INVALID_ARG, "coarsest level matrix is singular");
+        if (p != c) {
+            std::swap_ranges(a.begin() + c * n, a.begin() + c * n + n, a.begin() + p * n);
+            std::swap(perm[c], perm[p]);
+        }
+        const double piv = a[c * n + c];
+        for (int64_t i = c + 1; i < n; ++i) {
+            const double l = a[i * n + c] / piv;
+            a[i * n + c] = l;
+            if (l != 0.0)
+                for (int64_t j = c + 1; j < n; ++j) a[i * n + j] -= l * a[c * n + j];
+        }
+    }
+    inv.assign(n * n, 0.0);
+    std::vector<double> y(n);
+    for (int64_t e = 0; e < n; ++e) {  // column e of A^{-1}: solve A x = e_e
+        for (int64_t i = 0; i < n; ++i) {
+            double v = (perm[i] == e) ? 1.0 : 0.0;
+            for (int64_t j = 0; j < i; ++j) v -= a[i * n + j] * y[j];
+            y[i] = v;
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double v = y[i];
+            for (int64_t j = i + 1; j < n; ++j) v -= a[i * n + j] * y[j];
+            y[i] = v / a[i * n + i];
+        }
+        for (int64_t i = 0; i < n; ++i) inv[i * n + e] = y[i];
+    }
+}
+
+// Greedy row blocks for the SpMV kernel: consecutive rows while the block
+// stays within rows_cap rows and nnz_cap nonzeros (a longer single row gets a
+// block of its own and is processed in several shared-memory tiles).
+std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_cap, int nnz_cap) {
+    const int64_t n = (int64_t)ptr.size() - 1;
+    std::vector<int32_t> blk;
+    blk.reserve(n / 8 + 2);
+    blk.push_back(0);
+    int64_t start = 0;
+    while (start < n) {
+        int64_t end = start + 1;
+        while (end < n && end - start < rows_cap && ptr[end + 1] - ptr[start] <= nnz_cap) ++end;
+        blk.push_back((int32_t)end);
+        start = end;
+    }
+    return blk;
+}
+
+}  // namespace amg

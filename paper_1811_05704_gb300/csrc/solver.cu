@@ -1,0 +1,553 @@
+// solver.cu -- hierarchy construction (Algorithm 1), the V-cycle (Algorithm 2)
+// and the Krylov loops, issued either as one CUDA graph per solve (a
+// device-side while-node runs the iterations; the loop condition is set by
+// the kernel that computes the residual norm) or as host-driven launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+#include "amg_internal.h"
+#include "handle.h"
+
+namespace amg {
+
+// ------------------------------------------------------------ memory
+template <typename T>
+static T* halloc(amg_handle* h, size_t count) {
+    T* p = dev_alloc<T>(count > 0 ? count : 1);
+    h->dev_allocs.push_back(p);
+    return p;
+}
+
+static void track(amg_handle* h, const DevCsr& D) {
+    h->dev_allocs.push_back(D.ptr);
+    h->dev_allocs.push_back(D.col);
+    h->dev_allocs.push_back(D.val);
+}
+
+static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D) {
+    const std::vector<int32_t> blk = host_row_blocks(ptr, kRowsPerBlock, kTileNnz);
+    D.nblk = (int32_t)blk.size() - 1;
+    D.blk = halloc<int32_t>(h, blk.size());
+    AMG_CUDA(cudaMemcpy(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+}
+
+static void make_f32(amg_handle* h, DevCsr& D) {
+    D.val32 = halloc<float>(h, D.nnz);
+    launch_copy_to_f32(D.val, D.val32, D.nnz, h->stream);
+}
+
+static void upload(amg_handle* h, const HostCsr& H, DevCsr& D) {
+    D.nrows = (int32_t)H.nrows;
+    D.ncols = (int32_t)H.ncols;
+    D.nnz = H.nnz();
+    D.ptr = halloc<int32_t>(h, H.nrows + 1);
+    D.col = halloc<int32_t>(h, D.nnz);
+    D.val = halloc<double>(h, D.nnz);
+    AMG_CUDA(cudaMemcpy(D.ptr, H.ptr.data(), (H.nrows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    AMG_CUDA(cudaMemcpy(D.col, H.col.data(), D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    AMG_CUDA(cudaMemcpy(D.val, H.val.data(), D.nnz * sizeof(double), cudaMemcpyHostToDevice));
+    schedule(h, H.ptr, D);
+}
+
+static void download(const DevCsr& D, HostCsr& H) {
+    H.nrows = D.nrows;
+    H.ncols = D.ncols;
+    H.ptr.resize(D.nrows + 1);
+    H.col.resize(D.nnz);
+    H.val.resize(D.nnz);
+    AMG_CUDA(cudaMemcpy(H.ptr.data(), D.ptr, (D.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    AMG_CUDA(cudaMemcpy(H.col.data(), D.col, D.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    AMG_CUDA(cudaMemcpy(H.val.data(), D.val, D.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+// ------------------------------------------------------------- setup
+// Algorithm 1.  Stop rule: a level with at most coarse_enough rows, the
+// max_levels-th level, or a level whose aggregation keeps >= 95% of the rows
+// is the coarsest; a stall on a level larger than max_coarse_dense is an
+// error, and so is a coarsest level larger than max_coarse_dense.
+void build_hierarchy(amg_handle* h, HostCsr A) {
+    const amg_params& prm = h->prm;
+    const bool f32 = prm.precision == AMG_PRECISION_FP32;
+    h->lev.clear();
+    h->lev.reserve(AMG_MAX_LEVELS + 1);  // references to levels stay valid below
+    h->lev.emplace_back();
+    upload(h, A, h->lev[0].A);
+    for (int l = 0;; ++l) {
+        Level& L = h->lev[l];
+        const int64_t n = A.nrows;
+        const std::vector<double> dg = host_diagonal(A);
+        host_smoother_diag(A, dg, prm, L.dhost);
+        L.d = halloc<double>(h, n);
+        AMG_CUDA(cudaMemcpy(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        bool coarsest = n <= prm.coarse_enough || l + 1 >= prm.max_levels || l + 1 >= AMG_MAX_LEVELS;
+        if (!coarsest) {
+            double eps = prm.strength_eps;
+            if (prm.strength_halving)
+                for (int q = 0; q < l; ++q) eps *= 0.5;
+            L.nagg = host_aggregate(A, dg, eps, L.agg);
+            if ((double)L.nagg >= 0.95 * (double)n) {
+                L.agg.clear();
+                L.nagg = 0;
+                if (n > prm.max_coarse_dense)
+                    fail(AMG_ERR_COARSENING_STALLED,
+                         "aggregation stalled on level " + std::to_string(l) + " with " +
+                             std::to_string(n) + " rows");
+                coarsest = true;
+            } else {
+                HostCsr P, R;
+                host_prolongation(A, dg, eps, L.agg, L.nagg, P, L.omega_p);
+                host_transpose(P, R);
+                upload(h, P, L.P);
+                upload(h, R, L.R);
+                DevCsr AP, Ac;
+                device_spgemm(L.A, L.P, AP, h->stream);
+                try {
+                    device_spgemm(L.R, AP, Ac, h->stream);
+                } catch (...) {
+                    dev_free(AP.ptr); dev_free(AP.col); dev_free(AP.val);
+                    throw;
+                }
+                dev_free(AP.ptr); dev_free(AP.col); dev_free(AP.val);
+                track(h, Ac);
+                HostCsr next;
+                download(Ac, next);
+                schedule(h, next.ptr, Ac);
+                if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
+                h->lev.emplace_back();
+                h->lev.back().A = Ac;
+                A = std::move(next);
+            }
+        }
+        if (f32) {
+            make_f32(h, L.A);
+            L.d32 = halloc<float>(h, n);
+            std::vector<float> d32(L.dhost.begin(), L.dhost.end());
+            AMG_CUDA(cudaMemcpy(L.d32, d32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        if (coarsest) {
+            if (n > prm.max_coarse_dense)
+                fail(AMG_ERR_TOO_LARGE, "coarsest level has " + std::to_string(n) +
+                                            " rows, above max_coarse_dense");
+            std::vector<double> inv;
+            host_dense_inverse(A, inv);
+            h->nc = (int32_t)n;
+            h->cinv = halloc<double>(h, inv.size());
+            AMG_CUDA(cudaMemcpy(h->cinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+            break;
+        }
+    }
+    // level vectors
+    const int nl = (int)h->lev.size();
+    for (int l = 0; l < nl; ++l) {
+        Level& L = h->lev[l];
+        const int64_t n = L.A.nrows;
+        const bool last = l == nl - 1;
+        if (nl == 1) break;
+        if (l > 0) L.f = halloc<double>(h, n);
+        L.x = halloc<double>(h, n);
+        if (!last) { L.y = halloc<double>(h, n); L.t = halloc<double>(h, n); }
+        if (f32) {
+            if (l > 0) L.f32 = halloc<float>(h, n);
+            L.x32 = halloc<float>(h, n);
+            if (!last) { L.y32 = halloc<float>(h, n); L.t32 = halloc<float>(h, n); }
+        }
+    }
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ------------------------------------------------------------ issuing
+void Issue::pre(int kc) {
+    cur = kc;
+    ++launches;
+    if (!profile) return;
+    while (pool->size() < pool_used + 2) {
+        cudaEvent_t e;
+        AMG_CUDA(cudaEventCreate(&e));
+        pool->push_back(e);
+    }
+    cudaEvent_t a = (*pool)[pool_used++], b = (*pool)[pool_used++];
+    AMG_CUDA(cudaEventRecord(a, s));
+    events->push_back({kc, {a, b}});
+}
+
+void Issue::post() {
+    if (!profile) return;
+    AMG_CUDA(cudaEventRecord(events->back().second.second, s));
+}
+
+static const int* flag_ptr(amg_handle* h, size_t off) {
+    return reinterpret_cast<const int*>(reinterpret_cast<const char*>(h->st) + off);
+}
+
+// One V-cycle, z = M r (Algorithm 2 body with zero initial guess on every
+// level).  `rz`, if given, reduces r.z (fused into the last kernel).
+static void issue_vcycle64(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
+                           const Reduce* rz) {
+    std::vector<Level>& L = h->lev;
+    const int nl = (int)L.size();
+    const int npre = h->prm.npre, npost = h->prm.npost;
+    cudaStream_t s = I.s;
+    std::vector<double*> cur(nl, nullptr);
+    for (int l = 0; l < nl - 1; ++l) {
+        Level& v = L[l];
+        const int64_t n = v.A.nrows;
+        const double* f = (l == 0) ? r : v.f;
+        const int kcp = l == 0 ? AMG_KC_PRESMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
+        const int kcr = l == 0 ? AMG_KC_RESTRICT_L0 : AMG_KC_VCYCLE_COARSER;
+        if (npre == 0) {
+            I.pre(kcp); launch_fill(v.x, 0.0, n, s); I.post();
+            I.pre(kcr); launch_spmv(v.R, f, L[l + 1].f, skip, s); I.post();
+            cur[l] = v.x;
+            continue;
+        }
+        if (npre == 1) {
+            I.pre(kcp); launch_presmooth_residual(v.A, v.d, f, v.x, v.t, skip, s); I.post();
+            cur[l] = v.x;
+        } else {
+            I.pre(kcp); launch_scale(v.d, f, v.x, n, skip, s); I.post();
+            double* a = v.x;
+            for (int k = 1; k < npre; ++k) {
+                double* b = (a == v.x) ? v.y : v.x;
+                I.pre(kcp); launch_smooth(v.A, v.d, f, a, b, nullptr, nullptr, skip, s); I.post();
+                a = b;
+            }
+            I.pre(kcp); launch_residual_plain(v.A, f, a, v.t, skip, s); I.post();
+            cur[l] = a;
+        }
+        I.pre(kcr); launch_spmv(v.R, v.t, L[l + 1].f, skip, s); I.post();
+    }
+    if (nl == 1) {
+        I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve(h->cinv, h->nc, r, z, skip, s); I.post();
+        if (rz) { I.pre(AMG_KC_OTHER); launch_dot2(*rz, r, z, nullptr, nullptr, h->n, skip, s); I.post(); }
+        return;
+    }
+    Level& c = L[nl - 1];
+    I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve(h->cinv, h->nc, c.f, c.x, skip, s); I.post();
+    std::vector<double*> out(nl, nullptr);
+    out[nl - 1] = c.x;
+    for (int l = nl - 2; l >= 0; --l) {
+        Level& v = L[l];
+        const double* f = (l == 0) ? r : v.f;
+        const int kc = l == 0 ? AMG_KC_PROLONG_L0 : AMG_KC_VCYCLE_COARSER;
+        const int kcs = l == 0 ? AMG_KC_POSTSMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
+        double* a = cur[l];
+        I.pre(kc); launch_prolong_add(v.P, out[l + 1], a, skip, s); I.post();
+        if (npost == 0) {
+            if (l == 0) {
+                I.pre(AMG_KC_OTHER);
+                AMG_CUDA(cudaMemcpyAsync(z, a, v.A.nrows * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                I.post();
+                if (rz) { I.pre(AMG_KC_OTHER); launch_dot2(*rz, r, z, nullptr, nullptr, h->n, skip, s); I.post(); }
+            }
+            out[l] = a;
+            continue;
+        }
+        for (int k = 0; k < npost; ++k) {
+            const bool last = k == npost - 1;
+            double* b = (last && l == 0) ? z : ((a == v.x) ? v.y : v.x);
+            const Reduce* red = (last && l == 0) ? rz : nullptr;
+            I.pre(kcs); launch_smooth(v.A, v.d, f, a, b, red ? r : nullptr, red, skip, s); I.post();
+            a = b;
+        }
+        out[l] = a;
+    }
+}
+
+// float32 V-cycle (one pre- and one post-sweep); the finest level reads r and
+// writes z in float64, and r.z is reduced in float64.
+static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
+                           const Reduce* rz) {
+    std::vector<Level>& L = h->lev;
+    const int nl = (int)L.size();
+    cudaStream_t s = I.s;
+    if (nl == 1) { issue_vcycle64(h, I, r, z, skip, rz); return; }
+    for (int l = 0; l < nl - 1; ++l) {
+        Level& v = L[l];
+        const int kcp = l == 0 ? AMG_KC_PRESMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
+        const int kcr = l == 0 ? AMG_KC_RESTRICT_L0 : AMG_KC_VCYCLE_COARSER;
+        I.pre(kcp);
+        launch_presmooth_residual_f32(v.A, v.d32, l == 0 ? nullptr : v.f32, l == 0 ? r : nullptr,
+                                      v.x32, v.t32, skip, s);
+        I.post();
+        I.pre(kcr); launch_spmv_f32(v.R, v.t32, L[l + 1].f32, skip, s); I.post();
+    }
+    Level& c = L[nl - 1];
+    I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve_f32(h->cinv, h->nc, c.f32, c.x32, skip, s); I.post();
+    const float* below = c.x32;
+    for (int l = nl - 2; l >= 0; --l) {
+        Level& v = L[l];
+        const int kc = l == 0 ? AMG_KC_PROLONG_L0 : AMG_KC_VCYCLE_COARSER;
+        const int kcs = l == 0 ? AMG_KC_POSTSMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
+        I.pre(kc); launch_prolong_add_f32(v.P, below, v.x32, skip, s); I.post();
+        I.pre(kcs);
+        launch_smooth_f32(v.A, v.d32, l == 0 ? nullptr : v.f32, l == 0 ? r : nullptr, v.x32,
+                          l == 0 ? nullptr : v.y32, l == 0 ? z : nullptr,
+                          (l == 0 && rz) ? r : nullptr, l == 0 ? rz : nullptr, skip, s);
+        I.post();
+        below = v.y32;
+    }
+}
+
+static void issue_vcycle(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
+                         const Reduce* rz) {
+    if (h->prm.precision == AMG_PRECISION_FP32) issue_vcycle32(h, I, r, z, skip, rz);
+    else issue_vcycle64(h, I, r, z, skip, rz);
+}
+
+static Reduce base_reduce(amg_handle* h) {
+    Reduce r;
+    r.partial = h->partial;
+    r.stride = h->stride;
+    r.counter = h->counter;
+    r.st = h->st;
+    return r;
+}
+
+static Reduce with(Reduce r, int fin) {
+    r.fin = fin;
+    return r;
+}
+
+// CG (Saad Alg. 9.1, preconditioned): init forms r = f - A x and the norms;
+// each pass of the body is z = M r (with r.z), p = z + beta p, q = A p (with
+// p.q), x += alpha p, r -= alpha q (with r.r and the loop test).
+static void cg_init(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
+    const DevCsr& A = h->lev[0].A;
+    I.pre(AMG_KC_OTHER); launch_residual(A, f, x, h->r, nullptr, with(b, FIN_INIT), nullptr, I.s); I.post();
+    I.pre(AMG_KC_OTHER); launch_fill(h->p, 0.0, h->n, I.s); I.post();
+}
+
+static void cg_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
+    const DevCsr& A = h->lev[0].A;
+    const int* halt = flag_ptr(h, offsetof(KState, halt));
+    const Reduce rz = with(b, FIN_CG_RHO);
+    issue_vcycle(h, I, h->r, h->z, halt, &rz);
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_pupdate(h->st, h->z, h->p, h->n, I.s); I.post();
+    I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot(A, h->p, nullptr, h->q, with(b, FIN_CG_ALPHA), halt, I.s); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_update(with(b, FIN_CG_RES), h->p, h->q, x, h->r, h->n, I.s); I.post();
+}
+
+// BiCGStab (van der Vorst; right-preconditioned, Saad Alg. 7.7).
+static void bi_init(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
+    const DevCsr& A = h->lev[0].A;
+    I.pre(AMG_KC_OTHER); launch_residual(A, f, x, h->r, h->rh, with(b, FIN_BI_INIT), nullptr, I.s); I.post();
+    I.pre(AMG_KC_OTHER); launch_fill(h->p, 0.0, h->n, I.s); I.post();
+    I.pre(AMG_KC_OTHER); launch_fill(h->v, 0.0, h->n, I.s); I.post();
+}
+
+static void bi_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
+    const DevCsr& A = h->lev[0].A;
+    const int* halt = flag_ptr(h, offsetof(KState, halt));
+    const int* skip2 = flag_ptr(h, offsetof(KState, skip2));
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_pupdate(h->st, h->r, h->v, h->p, h->n, I.s); I.post();
+    issue_vcycle(h, I, h->p, h->ph, halt, nullptr);
+    I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot(A, h->ph, h->rh, h->v, with(b, FIN_BI_ALPHA), halt, I.s); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_s(with(b, FIN_BI_HALF), h->r, h->v, h->sv, h->n, I.s); I.post();
+    issue_vcycle(h, I, h->sv, h->sh, skip2, nullptr);
+    I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot2(A, h->sh, h->sv, h->tv, with(b, FIN_BI_OMEGA), skip2, I.s); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE);
+    launch_bi_update(with(b, FIN_BI_RES), h->rh, h->ph, h->sh, h->sv, h->tv, x, h->r, h->n, I.s);
+    I.post();
+}
+
+static void issue_init(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
+    if (h->prm.solver == AMG_SOLVER_BICGSTAB) bi_init(h, I, f, x, b);
+    else cg_init(h, I, f, x, b);
+}
+
+static void issue_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
+    if (h->prm.solver == AMG_SOLVER_BICGSTAB) bi_body(h, I, x, b);
+    else cg_body(h, I, x, b);
+}
+
+static void issue_post(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
+    I.pre(AMG_KC_OTHER);
+    launch_residual(h->lev[0].A, f, x, h->r, nullptr, with(b, FIN_TRUE), nullptr, I.s);
+    I.post();
+}
+
+// --------------------------------------------------------------- graphs
+static void destroy_graph(CachedGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+}
+
+void destroy_graphs(amg_handle* h) {
+    for (CachedGraph& g : h->graphs) destroy_graph(g);
+    h->graphs.clear();
+}
+
+// Capture [state upload] -> init -> while(cond){ body } -> true residual ->
+// [state download] for one (f, x) pair.  The while-node's condition is set
+// on the device by the kernels that finish each iteration.
+static CachedGraph capture(amg_handle* h, const double* f, double* x) {
+    CachedGraph g;
+    g.f = f;
+    g.x = x;
+    cudaStream_t cs = h->cap;
+    AMG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    bool capturing = true, capturing2 = false;
+    try {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edata = nullptr;
+        size_t ndeps = 0;
+        AMG_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, &edata, &ndeps));
+        cudaGraphConditionalHandle hc;
+        AMG_CUDA(cudaGraphConditionalHandleCreate(&hc, capg, 0, cudaGraphCondAssignDefault));
+        Reduce b = base_reduce(h);
+        b.set_cond = 1;
+        b.cond_handle = (unsigned long long)hc;
+        AMG_CUDA(cudaMemcpyAsync(h->st, h->st_in, sizeof(KState), cudaMemcpyHostToDevice, cs));
+        Issue I;
+        I.s = cs;
+        issue_init(h, I, f, x, b);
+        g.init_launches = I.launches;
+
+        AMG_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, &edata, &ndeps));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        AMG_CUDA(cudaGraphAddNode(&cnode, capg, deps, edata, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        AMG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies));
+        AMG_CUDA(cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        capturing2 = true;
+        Issue I2;
+        I2.s = h->cap2;
+        issue_body(h, I2, x, b);
+        g.body_launches = I2.launches;
+        cudaGraph_t tmp = nullptr;
+        capturing2 = false;
+        AMG_CUDA(cudaStreamEndCapture(h->cap2, &tmp));
+
+        Issue I3;
+        I3.s = cs;
+        issue_post(h, I3, f, x, b);
+        g.post_launches = I3.launches;
+        AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, cs));
+        capturing = false;
+        AMG_CUDA(cudaStreamEndCapture(cs, &g.graph));
+        AMG_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        if (capturing2) cudaStreamEndCapture(h->cap2, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        tmp = nullptr;
+        if (capturing) cudaStreamEndCapture(cs, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        destroy_graph(g);
+        cudaGetLastError();
+        throw;
+    }
+    return g;
+}
+
+static CachedGraph& graph_for(amg_handle* h, const double* f, double* x) {
+    for (CachedGraph& g : h->graphs)
+        if (g.f == f && g.x == x) return g;
+    if (h->graphs.size() >= 4) {
+        destroy_graph(h->graphs.front());
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(capture(h, f, x));
+    return h->graphs.back();
+}
+
+// ----------------------------------------------------------------- solve
+// One attempt: (graph | host loop) -> st_out.  Returns launches issued.
+static int64_t attempt(amg_handle* h, const double* f, double* x, bool use_graph, Issue* prof) {
+    if (use_graph) {
+        CachedGraph* gp = nullptr;
+        try {
+            gp = &graph_for(h, f, x);
+        } catch (const Error& e) {
+            // the graph could not be built (e.g. conditional nodes refused):
+            // run the same kernels from the host from now on
+            h->graph_unsupported = true;
+            destroy_graphs(h);
+            return attempt(h, f, x, false, prof);
+        }
+        CachedGraph& g = *gp;
+        const int it0 = h->st_in->it;
+        AMG_CUDA(cudaGraphLaunch(g.exec, h->stream));
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        const int64_t iters = std::max(0, h->st_out->it - it0);
+        return g.init_launches + iters * g.body_launches + g.post_launches;
+    }
+    Issue local;
+    Issue& I = prof ? *prof : local;
+    I.s = h->stream;
+    const int64_t l0 = I.launches;
+    Reduce b = base_reduce(h);
+    AMG_CUDA(cudaMemcpyAsync(h->st, h->st_in, sizeof(KState), cudaMemcpyHostToDevice, h->stream));
+    issue_init(h, I, f, x, b);
+    AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    int guard = 0;
+    while (h->st_out->cond && guard++ <= h->st_in->maxiter + 1) {
+        issue_body(h, I, x, b);
+        AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->stream));
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    issue_post(h, I, f, x, b);
+    AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    return I.launches - l0;
+}
+
+amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int maxiter,
+                     int* iters, double* relres, Issue* prof) {
+    if (!f || !x) fail(AMG_ERR_INVALID_ARG, "f and x must be device pointers");
+    if (!(rtol >= 0.0) || maxiter < 0) fail(AMG_ERR_INVALID_ARG, "rtol must be >= 0 and maxiter >= 0");
+    if (f == x) fail(AMG_ERR_INVALID_ARG, "f and x must be distinct buffers");
+    std::memset(h->st_in, 0, sizeof(KState));
+    h->st_in->rtol = rtol;
+    h->st_in->maxiter = maxiter;
+    bool use_graph = h->prm.use_graph && !h->graph_unsupported && !prof;
+    int64_t launches = 0;
+    amg_status status = AMG_OK;
+    for (int attempt_no = 0; attempt_no < 64; ++attempt_no) {
+        launches += attempt(h, f, x, use_graph && !h->graph_unsupported, prof);
+        const KState& o = *h->st_out;
+        if (o.zero_rhs) {
+            AMG_CUDA(cudaMemsetAsync(x, 0, h->n * sizeof(double), h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+            if (iters) *iters = 0;
+            if (relres) *relres = 0.0;
+            h->last_launches = launches;
+            return AMG_OK;
+        }
+        if (o.status == AMG_ERR_BREAKDOWN) { status = AMG_ERR_BREAKDOWN; break; }
+        if (o.relres <= rtol) { status = AMG_OK; break; }
+        if (o.it >= maxiter) { status = AMG_ERR_NOT_CONVERGED; break; }
+        // the recurrence met rtol but the true residual did not: restart
+        h->st_in->it = o.it;
+        status = AMG_ERR_NOT_CONVERGED;
+    }
+    if (iters) *iters = h->st_out->it;
+    if (relres) *relres = h->st_out->relres;
+    h->last_launches = launches;
+    return status;
+}
+
+void run_vcycle(amg_handle* h, const double* r, double* z) {
+    Issue I;
+    I.s = h->stream;
+    issue_vcycle(h, I, r, z, nullptr, nullptr);
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+}  // namespace amg

@@ -1,0 +1,352 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances (derived in the design notes):
+  * aggregates, sparsity patterns of P, R and A_l: bit-exact;
+  * values of P, R, A_l and the smoother diagonal: bit-exact (the host setup
+    and the GPU Galerkin product evaluate every entry in the oracle's order
+    without FMA contraction);
+  * one SpMV row: |y - y_ref| <= 64 u sum_j |a_ij x_j| (u = 2^-53);
+  * one V-cycle: ||z - z_ref|| <= 1e-10 ||z_ref||;
+  * solves: true FP64 residual <= rtol = 1e-8, ||x - x_ref|| <= 1e-6 ||x_ref||,
+    iterations within +-1 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("_b", os.path.join(root, "paper_1811_05704_gb300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    b.build()
+    import paper_1811_05704_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    assert torch.cuda.is_available()
+    return torch, torch.device("cuda:0")
+
+
+def orc_params(**kw):
+    import oracle
+    m = {"strength_eps": "eps_strong", "strength_halving": "eps_halving"}
+    keep = {"eps_strong", "eps_halving", "smoother", "jacobi_omega", "npre", "npost",
+            "coarse_enough", "max_levels", "max_coarse_dense"}
+    p = {}
+    for k, v in kw.items():
+        k = m.get(k, k)
+        if k in keep:
+            p[k] = v
+    return oracle.default_params(**p)
+
+
+def both(amg, A, **kw):
+    import oracle
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, **kw)
+    H = oracle.Hierarchy(A, params=orc_params(**kw))
+    return S, H
+
+
+CASES = {
+    "poisson32": (lambda: gen.poisson3d(32), {}),
+    "poisson17": (lambda: gen.poisson3d(17), {"coarse_enough": 60}),
+    "varcoef20": (lambda: gen.varcoef3d(20, seed=1), {"coarse_enough": 100}),
+    "convdiff18": (lambda: gen.convdiff3d(18, seed=2)[0], {"solver": 1, "coarse_enough": 100}),
+    "poisson2d_101": (lambda: gen.poisson2d_shift(101, 0.05), {"coarse_enough": 100}),
+    "spai0_varcoef": (lambda: gen.varcoef3d(16, seed=3), {"smoother": 1, "coarse_enough": 50}),
+}
+
+
+def t(torch_dev, a):
+    torch, dev = torch_dev
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hierarchy_bit_exact(amg, case):
+    make, kw = CASES[case]
+    A = make()
+    S, H = both(amg, A, **kw)
+    info = S.info()
+    assert info["levels"] == H.levels >= 2
+    for l in range(H.levels):
+        oi = H.level_info(l)
+        assert info["rows"][l] == oi["n"] and info["nnz"][l] == oi["nnz"]
+        ptr, col, val, _ = amg.amg_get_level_matrix(S.handle, l, "A")
+        optr, ocol, oval, _ = H.matrix(l, "A")
+        assert np.array_equal(ptr, optr) and np.array_equal(col, ocol)
+        assert np.array_equal(val, oval), f"A_{l} values differ: {np.abs(val - oval).max()}"
+        assert np.array_equal(amg.amg_get_smoother_diag(S.handle, l), H.smoother_diagonal(l))
+        if l == H.levels - 1:
+            continue
+        assert np.array_equal(amg.amg_get_aggregates(S.handle, l), H.aggregates(l))
+        for w in "PR":
+            ptr, col, val, _ = amg.amg_get_level_matrix(S.handle, l, w)
+            optr, ocol, oval, _ = H.matrix(l, w)
+            assert np.array_equal(ptr, optr) and np.array_equal(col, ocol)
+            assert np.array_equal(val, oval), f"{w}_{l} values differ"
+    S.close()
+
+
+def _row_bound(ptr, col, val, x):
+    rows = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+    return np.bincount(rows, weights=np.abs(val * x[col]), minlength=len(ptr) - 1)
+
+
+@pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18"])
+def test_level_spmv(amg, torch_dev, case):
+    import oracle
+    make, kw = CASES[case]
+    A = make()
+    S, H = both(amg, A, **kw)
+    rng = np.random.default_rng(7)
+    for l in range(H.levels):
+        for w in ("A", "P", "R") if l < H.levels - 1 else ("A",):
+            ptr, col, val, (nr, nc) = H.matrix(l, w)
+            x = rng.uniform(-1, 1, nc)
+            y = t(torch_dev, np.zeros(nr))
+            amg.amg_level_spmv(S.handle, l, w, t(torch_dev, x), y)
+            yo = oracle.spmv(nr, nc, ptr.astype(np.int32), col, val, x)
+            bound = 64 * U * _row_bound(ptr, col, val, x)
+            assert np.all(np.abs(y.cpu().numpy() - yo) <= bound), (l, w)
+    S.close()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_vcycle(amg, torch_dev, case):
+    make, kw = CASES[case]
+    A = make()
+    S, H = both(amg, A, **kw)
+    r = gen.uniform_pm1(5, 20, A.n)
+    z = t(torch_dev, np.zeros(A.n))
+    amg.amg_apply_precond(S.handle, t(torch_dev, r), z)
+    zo = H.vcycle(r)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err <= 1e-10, err
+    S.close()
+
+
+@pytest.mark.parametrize("npre,npost", [(2, 0), (0, 2), (2, 3)])
+def test_vcycle_sweep_variants(amg, torch_dev, npre, npost):
+    A = gen.varcoef3d(14, seed=4)
+    S, H = both(amg, A, coarse_enough=40, npre=npre, npost=npost)
+    r = gen.uniform_pm1(6, 20, A.n)
+    z = t(torch_dev, np.zeros(A.n))
+    amg.amg_apply_precond(S.handle, t(torch_dev, r), z)
+    zo = H.vcycle(r)
+    assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+    S.close()
+
+
+def _true_relres(A, x, f):
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    Ax = np.bincount(rows, weights=A.val * x[A.col], minlength=A.n)
+    return np.linalg.norm(f - Ax) / np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_solve_matches_oracle(amg, torch_dev, case):
+    make, kw = CASES[case]
+    A = make()
+    S, H = both(amg, A, **kw)
+    f, ustar = gen.rhs_from_solution(A, 11)
+    x = t(torch_dev, np.zeros(A.n))
+    st, it, rr = S.solve(t(torch_dev, f), x, rtol=1e-8, maxiter=300)
+    xs = x.cpu().numpy()
+    solve = H.bicgstab if kw.get("solver") == 1 else H.cg
+    xo, ito, rro, sto = solve(f, rtol=1e-8, maxiter=300)
+    assert st == 0 and sto == 0
+    assert rr <= 1e-8 and _true_relres(A, xs, f) <= 1e-8
+    assert abs(rr - _true_relres(A, xs, f)) <= 1e-12
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert amg.amg_last_launch_count(S.handle) > 0
+    S.close()
+
+
+def test_graph_and_host_loop_agree_bitwise(amg, torch_dev):
+    A = gen.varcoef3d(18, seed=9)
+    f, _ = gen.rhs_from_solution(A, 1)
+    xs = []
+    for use_graph in (1, 0):
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val, coarse_enough=80, use_graph=use_graph)
+        x = t(torch_dev, np.zeros(A.n))
+        st, it, rr = S.solve(t(torch_dev, f), x)
+        xs.append((x.cpu().numpy(), it, rr))
+        S.close()
+    assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
+
+
+def test_repeat_solves_deterministic_and_host_buffers(amg, torch_dev):
+    A = gen.poisson3d(24)
+    f, _ = gen.rhs_from_solution(A, 2)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+    ft = t(torch_dev, f)
+    out = []
+    for _ in range(3):
+        x = t(torch_dev, np.zeros(A.n))
+        out.append((S.solve(ft, x), x.cpu().numpy()))
+    assert all(np.array_equal(out[0][1], o[1]) and out[0][0] == o[0] for o in out)
+    xh = np.zeros(A.n)
+    res = amg.amg_solve_host(S.handle, np.ascontiguousarray(f), xh)
+    assert res == out[0][0] and np.array_equal(xh, out[0][1])
+    S.close()
+
+
+def test_profile_solve_same_result(amg, torch_dev):
+    A = gen.poisson3d(20)
+    f, _ = gen.rhs_from_solution(A, 3)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, coarse_enough=100)
+    x1 = t(torch_dev, np.zeros(A.n))
+    r1 = S.solve(t(torch_dev, f), x1)
+    x2 = t(torch_dev, np.zeros(A.n))
+    st, it, rr, ms, ln = amg.amg_solve_profile(S.handle, t(torch_dev, f), x2)
+    assert (st, it, rr) == r1 and np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    assert ln["spmv_dot"] == it and ln["postsmooth_l0"] == it and ms["spmv_dot"] > 0
+    S.close()
+
+
+def test_standalone_spmv_dot(amg, torch_dev):
+    import oracle
+    torch, dev = torch_dev
+    for A in (gen.poisson3d(30), gen.varcoef3d(11, seed=2), gen.poisson2d_shift(7, 0.0)):
+        x = gen.uniform_pm1(1, 21, A.n)
+        rp, cl, vl = (torch.from_numpy(a).to(dev) for a in (A.row_ptr, A.col, A.val))
+        csr = amg.make_csr(A.n, rp, cl, vl)
+        y = t(torch_dev, np.zeros(A.n))
+        d = t(torch_dev, np.zeros(1))
+        amg.amg_spmv_dot(csr, t(torch_dev, x), y, d)
+        yo = oracle.spmv(A.n, A.n, A.row_ptr, A.col, A.val, x)
+        assert np.all(np.abs(y.cpu().numpy() - yo) <= 64 * U * _row_bound(A.row_ptr, A.col, A.val, x))
+        do = float(x @ yo)
+        assert abs(d.item() - do) <= 1e-12 * np.abs(x * yo).sum()
+    # broken structure is refused, not read out of bounds
+    A = gen.poisson3d(6)
+    bad_ptr = A.row_ptr.copy()
+    bad_ptr[5] = bad_ptr[7]
+    bad_col = A.col.copy()
+    bad_col[3] = A.n + 5
+    for p_, c_ in ((bad_ptr, A.col), (A.row_ptr, bad_col)):
+        rp, cl, vl = (torch.from_numpy(a).to(dev) for a in (p_, c_, A.val))
+        y = t(torch_dev, np.zeros(A.n))
+        d = t(torch_dev, np.zeros(1))
+        with pytest.raises(amg.AmgError) as e:
+            amg.amg_spmv_dot(amg.make_csr(A.n, rp, cl, vl), t(torch_dev, np.ones(A.n)), y, d)
+        assert e.value.status == amg.AMG_ERR_INVALID_ARG
+
+
+def test_edge_cases(amg, torch_dev):
+    import oracle
+    # 1 x 1
+    S = amg.Solver(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    x = t(torch_dev, np.zeros(1))
+    assert S.solve(t(torch_dev, [8.0]), x) == (0, 1, 0.0) and x.item() == 2.0
+    S.close()
+    # single level (n <= coarse_enough): M = A^-1, one iteration
+    A = gen.poisson3d(7)
+    f, _ = gen.rhs_from_solution(A, 4)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+    assert S.info()["levels"] == 1
+    x = t(torch_dev, np.zeros(A.n))
+    st, it, rr = S.solve(t(torch_dev, f), x)
+    assert (st, it) == (0, 1) and rr <= 1e-12
+    S.close()
+    A = gen.poisson3d(12)
+    f, _ = gen.rhs_from_solution(A, 5)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, coarse_enough=50)
+    # f = 0 -> x = 0
+    x = t(torch_dev, np.ones(A.n))
+    assert S.solve(t(torch_dev, np.zeros(A.n)), x) == (0, 0, 0.0) and not x.any().item()
+    # maxiter = 0
+    x = t(torch_dev, np.zeros(A.n))
+    st, it, rr = S.solve(t(torch_dev, f), x, maxiter=0)
+    assert (st, it, rr) == (amg.AMG_ERR_NOT_CONVERGED, 0, 1.0)
+    # exact initial guess
+    xs = np.linalg.solve(A.to_dense(), f)
+    x = t(torch_dev, xs)
+    st, it, rr = S.solve(t(torch_dev, f), x)
+    assert st == 0 and it == 0
+    S.close()
+    # invalid inputs
+    bad = gen.poisson3d(4)
+    col = bad.col.copy()
+    col[1], col[2] = col[2], col[1]
+    with pytest.raises(amg.AmgError) as e:
+        amg.Solver(bad.n, bad.row_ptr, col, bad.val)
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    val = bad.val.copy()
+    val[bad.row_ptr[3] + 1] = 0.0  # diagonal of row 3 (one lower neighbour before it)
+    with pytest.raises(amg.AmgError) as e:
+        amg.Solver(bad.n, bad.row_ptr, bad.col, val)
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    # aggregation stall on a large diagonal matrix
+    n = 5000
+    with pytest.raises(amg.AmgError) as e:
+        amg.Solver(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    assert e.value.status == amg.AMG_ERR_COARSENING_STALLED
+    with pytest.raises(amg.AmgError) as e:
+        amg.Solver(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+
+
+def test_fp32_vcycle_reaches_fp64_tolerance(amg, torch_dev):
+    import oracle
+    for A, kw in ((gen.poisson3d(32), {}), (gen.varcoef3d(24, seed=6), {"coarse_enough": 100})):
+        f, _ = gen.rhs_from_solution(A, 8)
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=1, **kw)
+        x = t(torch_dev, np.zeros(A.n))
+        st, it, rr = S.solve(t(torch_dev, f), x, rtol=1e-8, maxiter=300)
+        xs = x.cpu().numpy()
+        H = oracle.Hierarchy(A, params=orc_params(**kw))
+        xo, ito, rro, sto = H.cg(f, rtol=1e-8, maxiter=300)
+        assert st == 0 and rr <= 1e-8 and _true_relres(A, xs, f) <= 1e-8
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert it <= ito + 3, (it, ito)
+        S.close()
+
+
+def test_full_size_poisson150(amg, torch_dev):
+    """The 150^3 workload the benchmark times: hierarchy sizes and sampled
+    rows against the oracle, the solve against the oracle's solve."""
+    import oracle
+    A = gen.poisson3d(150)
+    f, ustar = gen.rhs_from_solution(A, 0)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+    H = oracle.Hierarchy(A)
+    info = S.info()
+    assert info["levels"] == H.levels
+    for l in range(H.levels):
+        assert info["rows"][l] == H.level_info(l)["n"] and info["nnz"][l] == H.level_info(l)["nnz"]
+    # aggregates of the finest level, bit-exact
+    assert np.array_equal(amg.amg_get_aggregates(S.handle, 0), H.aggregates(0))
+    # sampled rows of the finest-level product
+    x = gen.uniform_pm1(3, 22, A.n)
+    y = t(torch_dev, np.zeros(A.n))
+    amg.amg_level_spmv(S.handle, 0, "A", t(torch_dev, x), y)
+    yg = y.cpu().numpy()
+    rows = np.random.default_rng(0).choice(A.n, 2000, replace=False)
+    for i in rows:
+        k = slice(A.row_ptr[i], A.row_ptr[i + 1])
+        assert abs(yg[i] - np.dot(A.val[k], x[A.col[k]])) <= 64 * U * np.abs(A.val[k] * x[A.col[k]]).sum()
+    xd = t(torch_dev, np.zeros(A.n))
+    st, it, rr = S.solve(t(torch_dev, f), xd, rtol=1e-8, maxiter=200)
+    xs = xd.cpu().numpy()
+    xo, ito, rro, sto = H.cg(f, rtol=1e-8, maxiter=200)
+    assert st == 0 and rr <= 1e-8 and _true_relres(A, xs, f) <= 1e-8
+    assert abs(it - ito) <= 1
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert np.linalg.norm(xs - ustar) <= 1e-5 * np.linalg.norm(ustar)
+    S.close()
