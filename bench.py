@@ -1,0 +1,389 @@
+"""Benchmark: CG + smoothed-aggregation AMG solve phase on 150^3 Poisson.
+
+Workload: 3D Poisson, 7-point stencil on a 150^3 grid (3,375,000 unknowns,
+23,490,000 nonzeros), f = A u* with seeded u* ~ U(-1,1), x0 = 0, CG
+preconditioned by one SA-AMG V-cycle (strength 0.08, damped Jacobi 0.72, one
+pre- and one post-sweep, coarsest <= 500 rows, dense coarsest solve), rtol 1e-8,
+FP64.  A step is one complete solve on the resident hierarchy (setup excluded,
+as in the metric).  The finest-level matrix alone (282 MB) exceeds the 129 MB
+L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "CG+SA-AMG solve s & HBM GB/s (150^3 Poisson, rtol 1e-8); solves/s, p50/p99"
+SIDE = 150
+RTOL = 1e-8
+MAXITER = 200
+SEED = 0
+WORKLOAD = "poisson3d-150^3 7-point, f = A u*, CG + SA-AMG (eps 0.08, Jacobi 0.72, 1/1 sweeps, coarse <= 500), rtol 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------ algorithmic bytes
+def kernel_bytes(info):
+    """Algorithmic DRAM bytes per launch of each finest-level kernel (FP64 values,
+    int32 indices and row pointers; every array touched once per kernel, the
+    gathered vector counted once)."""
+    n0, z0 = info["rows"][0], info["nnz"][0]
+    n1 = info["rows"][1] if info["levels"] > 1 else 0
+    zp = info["nnz_p"][0]
+    return {
+        "spmv_dot": 12 * z0 + 4 * n0 + 8 * n0 + 8 * n0,           # A, row_ptr, p, q
+        "presmooth_l0": 12 * z0 + 4 * n0 + 16 * n0 + 16 * n0,     # A, d f read, x t written
+        "restrict_l0": 12 * zp + 4 * n1 + 8 * n0 + 8 * n1,        # R, t, f_1
+        "prolong_l0": 12 * zp + 4 * n0 + 8 * n1 + 16 * n0,        # P, x_1, x read+write
+        "postsmooth_l0": 12 * z0 + 4 * n0 + 8 * n0 + 16 * n0 + 8 * n0,  # A, x, d f, z
+    }
+
+
+def bytes_per_iteration(info, coarse_n):
+    """Algorithmic bytes of one CG iteration (the kernels the solve launches)."""
+    b = 0
+    L = info["levels"]
+    for l in range(L - 1):
+        n, z, zp, nc = info["rows"][l], info["nnz"][l], info["nnz_p"][l], info["rows"][l + 1]
+        b += 12 * z + 4 * n + 32 * n                 # presmooth + residual
+        b += 12 * zp + 4 * nc + 8 * n + 8 * nc       # restrict
+        b += 12 * zp + 4 * n + 8 * nc + 16 * n       # prolong + correct
+        b += 12 * z + 4 * n + 32 * n                 # postsmooth
+    b += 8 * coarse_n * coarse_n + 16 * coarse_n     # dense coarsest solve
+    n0, z0 = info["rows"][0], info["nnz"][0]
+    b += 12 * z0 + 20 * n0                           # q = A p, p.q
+    b += 48 * n0 + 24 * n0                           # x, r update; p update
+    return b
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel_class):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel, or
+    None if the summary is missing or the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel_class}_poisson150.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_1811_05704_gb300", "csrc", "spmv.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("spmv_cu_sha256_16") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    A = gen.poisson3d(SIDE)
+    f, _ = gen.rhs_from_solution(A, SEED)
+    H = oracle.Hierarchy(A)
+    times, its = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        x, it, rr, st = H.cg(f, rtol=RTOL, maxiter=MAXITER)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            its.append(it)
+    total = sum(times)
+    value = len(times) / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "inputs larger than L2"},
+        "solve_s": statistics.median(times), "iterations": its[0],
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step one full 150^3 CG solve of the FP64 oracle (setup excluded)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline_sample():
+    """The FP64 oracle, single-threaded, on one full solve of the same workload."""
+    import oracle
+    A = gen.poisson3d(SIDE)
+    f, _ = gen.rhs_from_solution(A, SEED)
+    H = oracle.Hierarchy(A)
+    t0 = time.perf_counter()
+    x, it, rr, st = H.cg(f, rtol=RTOL, maxiter=MAXITER)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full 150^3 CG solve of the FP64 oracle ({it} iterations, "
+                      f"{dt:.2f} s, setup excluded)"}
+
+
+# ---------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import paper_1811_05704_gb300 as amg
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    A = gen.poisson3d(SIDE)
+    f, _ = gen.rhs_from_solution(A, SEED)
+    t0 = time.perf_counter()
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+    setup_s = time.perf_counter() - t0
+    info = S.info()
+    coarse_n = info["rows"][-1]
+    ft = torch.from_numpy(f).to(dev)
+    x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+
+    for _ in range(args.warmup):
+        x.zero_()
+        S.solve(ft, x, RTOL, MAXITER)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, device events on the launching stream
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches = 0
+    iters = []
+    ev[0].record(stream)
+    for k in range(args.steps):
+        x.zero_()
+        st, it, rr = S.solve(ft, x, RTOL, MAXITER)
+        ev[k + 1].record(stream)
+        launches += amg.amg_last_launch_count(S.handle)
+        iters.append(it)
+        assert st == 0 and rr <= RTOL, (st, rr)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_s = ev[0].elapsed_time(ev[-1]) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    value = world * args.steps / total_s
+    solve_s = statistics.median(step_ms) / 1e3
+    b_iter = bytes_per_iteration(info, coarse_n)
+    solve_gbs = b_iter * iters[0] / solve_s / 1e9
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    fh = torch.from_numpy(f).pin_memory()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    fnp, xnp = fh.numpy(), xh.numpy()
+    e2e_steps = max(3, args.steps // 2)
+    xnp[:] = 0.0
+    amg.amg_solve_host(S.handle, fnp, xnp, RTOL, MAXITER)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        xnp[:] = 0.0
+        amg.amg_solve_host(S.handle, fnp, xnp, RTOL, MAXITER)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * e2e_steps / e2e_s if world == 1 else None, "unit": "solves/s",
+           "h2d_bytes_per_step": 2 * 8 * A.n, "d2h_bytes_per_step": 8 * A.n,
+           "note": "amg_solve_host: f and x0 copied in, x copied out, inside the timed loop"}
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * e2e_steps / float(t.item())
+
+    # ---- per-kernel attribution: the same solve with an event pair around
+    # every launch on the handle's stream
+    x.zero_()
+    pst, pit, prr, ms, ln = amg.amg_solve_profile(S.handle, ft, x, RTOL, MAXITER)
+    kb = kernel_bytes(info)
+    dom = max(kb, key=lambda k: ms[k])
+    avg_ms = ms[dom] / max(1, ln[dom])
+    peak, peak_kind = peaks()
+    achieved = kb[dom] / (avg_ms / 1e3) / 1e9
+    traffic = committed_traffic(dom)
+    per_kernel = {k: {"launches": ln[k], "ms": round(ms[k], 4),
+                      "gbs": (round(kb[k] * ln[k] / (ms[k] / 1e3) / 1e9, 1) if k in kb and ms[k] > 0 else None)}
+                  for k in ms}
+
+    # ---- mixed precision form (float32 V-cycle under FP64 CG), same workload
+    mixed = None
+    if not args.no_mixed:
+        S32 = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=amg.AMG_PRECISION_FP32)
+        for _ in range(2):
+            x.zero_()
+            S32.solve(ft, x, RTOL, MAXITER)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(reps):
+            x.zero_()
+            st32, it32, rr32 = S32.solve(ft, x, RTOL, MAXITER)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1) / 1e3 / reps
+        mixed = {"value": 1.0 / t32, "unit": "solves/s", "solve_s": t32, "iterations": it32,
+                 "relres": rr32, "status": st32, "precision": "fp32 V-cycle, fp64 CG"}
+        S32.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator; the paper's 150^3 Poisson size, RHS A u*)",
+        "config": {"workload": WORKLOAD, "precision": "fp64", "levels": info["levels"],
+                   "rows": info["rows"], "nnz": info["nnz"],
+                   "l2": "no flush: inputs larger than L2 (finest A alone 282 MB > 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "solve_s": solve_s, "iterations": iters[0], "setup_s": setup_s,
+        "hbm_gbs": solve_gbs,
+        "bytes_per_iteration": b_iter,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": kb[dom],
+                     "avg_launch_ms": avg_ms, "timing": "CUDA events around every launch of an "
+                     "instrumented solve on the same stream, run right after the timed region"},
+        "solve_frac_of_peak": solve_gbs / peak,
+        "kernels": per_kernel,
+        "mixed": mixed,
+        "clocks": clock_info,
+        "cpu_baseline": cpu,
+    }
+    S.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -75,6 +75,12 @@ typedef struct {
     int precision;         /* [AMG_PRECISION_FP64] */
     int use_graph;         /* [1] run the Krylov loop as one CUDA graph with a device-side
                               while-node; 0 = host-driven launches (same kernels) */
+    int use_stream;        /* [1] sparse products stream the matrix through shared memory with
+                              bulk asynchronous copies (persistent kernels); 0 = row-chunk
+                              kernels with plain loads.  Results agree to rounding. */
+    int use_pdl;           /* [1] let consecutive sparse-product kernels overlap through
+                              programmatic dependent launch (process-wide setting, applied
+                              at each call that launches work) */
 } amg_params;
 
 /* A CSR matrix as passed in by the caller (see the conventions above). */

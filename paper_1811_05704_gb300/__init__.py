@@ -48,6 +48,8 @@ class amg_params(C.Structure):
         ("solver", C.c_int),
         ("precision", C.c_int),
         ("use_graph", C.c_int),
+        ("use_stream", C.c_int),
+        ("use_pdl", C.c_int),
     ]
 
 

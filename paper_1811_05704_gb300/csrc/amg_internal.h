@@ -46,6 +46,9 @@ void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const a
                         std::vector<double>& d);
 void host_dense_inverse(const HostCsr& A, std::vector<double>& inv);  // row-major n x n
 std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_cap, int nnz_cap);
+// streaming-engine tiles: (row, nonzero) boundaries and lanes per row; empty
+// if a row has more than nnz_cap nonzeros
+std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int& vw);
 
 // ---------------------------------------------------------- device CSR
 // Row-block schedule: block b of the SpMV kernel covers rows
@@ -62,9 +65,16 @@ struct DevCsr {
     int32_t* col = nullptr;
     double* val = nullptr;
     float* val32 = nullptr;  // float32 copy (mixed-precision V-cycle), optional
-    int32_t* blk = nullptr;  // row-block schedule
+    int32_t* blk = nullptr;  // row-block schedule (row-chunk engine)
     int32_t nblk = 0;
+    int2* tiles = nullptr;   // streaming-engine tiles {first row, first nonzero}, ntiles + 1
+    int32_t ntiles = 0;      // 0: some row is longer than a tile, use the row-chunk engine
+    int32_t vw = 1;          // lanes per row in the streaming engine
 };
+// Device CSR arrays carry kPad readable elements past their end (row_ptr
+// past n + 1, col/val past nnz): the streaming engine copies 16-byte-aligned
+// spans that may overrun the last row by up to three elements.
+constexpr int kPad = 8;
 
 // ------------------------------------------------------- Krylov state
 // Lives in device memory; scalars of the Krylov recurrences are computed on
@@ -132,6 +142,10 @@ void launch_residual_plain(const DevCsr& A, const double* f, const double* x, do
 void launch_scale(const double* d, const double* f, double* x, int64_t n, const int* skip,
                   cudaStream_t s);
 int vec_grid(int64_t n);
+int stream_grid(int ntiles);
+void set_stream_options(bool pdl);
+int read_and_clear_dev_err();
+void enqueue_dev_err_copy(int* host_dst, cudaStream_t s);
 // standalone, uniform rows-per-block schedule, bounds-checked columns
 void launch_spmv_dot_uniform(int32_t n, int32_t ncols, const int32_t* ptr, const int32_t* col,
                              const double* val, const double* x, double* y, int rows_per_block,

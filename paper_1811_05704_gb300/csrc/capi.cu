@@ -76,6 +76,7 @@ static void free_handle(amg_handle* h) {
     for (void* p : h->dev_allocs) cudaFree(p);
     if (h->st_in) cudaFreeHost(h->st_in);
     if (h->st_out) cudaFreeHost(h->st_out);
+    if (h->err_host) cudaFreeHost(h->err_host);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->cap2) cudaStreamDestroy(h->cap2);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
@@ -128,6 +129,8 @@ amg_status amg_params_default(amg_params* p) {
     p->solver = AMG_SOLVER_CG;
     p->precision = AMG_PRECISION_FP64;
     p->use_graph = 1;
+    p->use_stream = 1;
+    p->use_pdl = 1;
     return AMG_OK;
 }
 
@@ -181,9 +184,12 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             AMG_CUDA(cudaMemset(h->st, 0, sizeof(KState)));
             AMG_CUDA(cudaMallocHost(&h->st_in, sizeof(KState)));
             AMG_CUDA(cudaMallocHost(&h->st_out, sizeof(KState)));
+            AMG_CUDA(cudaMallocHost(&h->err_host, sizeof(int)));
+            *h->err_host = 0;
             std::memset(h->st_in, 0, sizeof(KState));
             std::memset(h->st_out, 0, sizeof(KState));
-            h->stride = std::max<int>(h->lev[0].A.nblk, vec_grid(h->n));
+            h->stride = std::max(std::max<int>(h->lev[0].A.nblk, vec_grid(h->n)),
+                                 stream_grid(std::max(1, h->lev[0].A.ntiles)));
             h->partial = dev_alloc<double>(2 * (size_t)h->stride);
             h->dev_allocs.push_back(h->partial);
             h->counter = dev_alloc<unsigned int>(1);
@@ -211,6 +217,7 @@ amg_status amg_solve(amg_handle* h, const double* f, double* x, double rtol, int
     return guarded([&]() -> amg_status {
         if (!h) fail(AMG_ERR_INVALID_ARG, "null handle");
         AMG_CUDA(cudaSetDevice(h->device));
+        set_stream_options(h->prm.use_pdl != 0);
         return run_solve(h, f, x, rtol, maxiter, iters, relres, nullptr);
     });
 }
@@ -220,6 +227,7 @@ amg_status amg_solve_host(amg_handle* h, const double* f_host, double* x_host, d
     return guarded([&]() -> amg_status {
         if (!h || !f_host || !x_host) fail(AMG_ERR_INVALID_ARG, "null argument");
         AMG_CUDA(cudaSetDevice(h->device));
+        set_stream_options(h->prm.use_pdl != 0);
         const size_t bytes = h->n * sizeof(double);
         AMG_CUDA(cudaMemcpyAsync(h->fbuf, f_host, bytes, cudaMemcpyHostToDevice, h->stream));
         AMG_CUDA(cudaMemcpyAsync(h->xbuf, x_host, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -235,6 +243,7 @@ amg_status amg_solve_profile(amg_handle* h, const double* f, double* x, double r
     return guarded([&]() -> amg_status {
         if (!h) fail(AMG_ERR_INVALID_ARG, "null handle");
         AMG_CUDA(cudaSetDevice(h->device));
+        set_stream_options(h->prm.use_pdl != 0);
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
         Issue I;
         I.s = h->stream;
@@ -319,6 +328,7 @@ amg_status amg_apply_precond(amg_handle* h, const double* r, double* z) {
     return guarded([&]() -> amg_status {
         if (!h || !r || !z || r == z) fail(AMG_ERR_INVALID_ARG, "bad arguments");
         AMG_CUDA(cudaSetDevice(h->device));
+        set_stream_options(h->prm.use_pdl != 0);
         run_vcycle(h, r, z);
         return AMG_OK;
     });
@@ -333,6 +343,7 @@ amg_status amg_level_spmv(amg_handle* h, int level, int which, const double* x, 
         if (!x || !y || x == y) fail(AMG_ERR_INVALID_ARG, "bad vectors");
         AMG_CUDA(cudaSetDevice(h->device));
         const DevCsr& D = which == 0 ? L.A : which == 1 ? L.P : L.R;
+        set_stream_options(h->prm.use_pdl != 0);
         launch_spmv(D, x, y, nullptr, h->stream);
         AMG_CUDA(cudaStreamSynchronize(h->stream));
         return AMG_OK;

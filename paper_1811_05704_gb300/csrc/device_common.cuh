@@ -19,8 +19,8 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Sum over the block (blockDim.x == kThreads) in a fixed order; the result
-// is valid in thread 0.  `sh` needs kThreads/32 doubles.
+// Sum over the block (blockDim.x a multiple of 32) in a fixed order; the
+// result is valid in thread 0.  `sh` needs blockDim.x/32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum(v);
@@ -29,8 +29,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
     }
     return t;
 }
@@ -151,7 +150,7 @@ __device__ void finalize(const Reduce& red, double a, double b) {
 // partials in index order and runs finalize().  Deterministic for a given
 // grid size.  Must be reached by every thread of every block of the grid.
 __device__ void reduce_finalize(const Reduce& red, double a, double b) {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[32];
     __shared__ int last;
     const double ta = block_sum(a, sh);
     const double tb = block_sum(b, sh);
@@ -166,7 +165,7 @@ __device__ void reduce_finalize(const Reduce& red, double a, double b) {
     if (!last) return;
     __threadfence();
     double sa = 0.0, sb = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) {
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         sa += __ldcg(red.partial + i);
         sb += __ldcg(red.partial + red.stride + i);
     }

@@ -65,6 +65,7 @@ struct amg_handle {
     amg::KState* st = nullptr;        // device
     amg::KState* st_in = nullptr;     // pinned host
     amg::KState* st_out = nullptr;    // pinned host
+    int* err_host = nullptr;          // pinned host copy of the device error word
     double* partial = nullptr;
     int stride = 0;
     unsigned int* counter = nullptr;

@@ -292,4 +292,27 @@ std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_c
     return blk;
 }
 
+// Tiles of the streaming engine: `vw` lanes share a row (a power of two
+// about a sixth of the mean row length, so each lane handles a handful of
+// nonzeros), at most kRowsPerBlock / vw rows and nnz_cap nonzeros per tile.
+// Returned as flattened (first row, first nonzero) pairs, one per tile plus
+// the end; empty if a single row exceeds nnz_cap.
+std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int& vw) {
+    const int64_t n = (int64_t)ptr.size() - 1;
+    int64_t longest = 0;
+    for (int64_t i = 0; i < n; ++i) longest = std::max<int64_t>(longest, ptr[i + 1] - ptr[i]);
+    if (longest > nnz_cap || n == 0) return {};
+    const double avg = (double)ptr[n] / (double)n;
+    vw = 1;
+    while (vw < 32 && 2.0 * vw <= avg / 6.0) vw *= 2;
+    const std::vector<int32_t> rows = host_row_blocks(ptr, kRowsPerBlock / vw, nnz_cap);
+    std::vector<int32_t> out;
+    out.reserve(2 * rows.size());
+    for (int32_t r : rows) {
+        out.push_back(r);
+        out.push_back(ptr[r]);
+    }
+    return out;
+}
+
 }  // namespace amg

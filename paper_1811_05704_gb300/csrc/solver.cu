@@ -33,10 +33,22 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D) 
     D.nblk = (int32_t)blk.size() - 1;
     D.blk = halloc<int32_t>(h, blk.size());
     AMG_CUDA(cudaMemcpy(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    int vw = 1;
+    const std::vector<int32_t> tiles = host_tiles(ptr, kTileNnz, vw);
+    D.tiles = nullptr;
+    D.ntiles = 0;
+    if (!tiles.empty() && h->prm.use_stream) {
+        D.ntiles = (int32_t)tiles.size() / 2 - 1;
+        D.vw = vw;
+        int32_t* t = halloc<int32_t>(h, tiles.size());
+        AMG_CUDA(cudaMemcpy(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        D.tiles = reinterpret_cast<int2*>(t);
+    }
 }
 
 static void make_f32(amg_handle* h, DevCsr& D) {
-    D.val32 = halloc<float>(h, D.nnz);
+    D.val32 = halloc<float>(h, D.nnz + kPad);
+    AMG_CUDA(cudaMemset(D.val32, 0, (D.nnz + kPad) * sizeof(float)));
     launch_copy_to_f32(D.val, D.val32, D.nnz, h->stream);
 }
 
@@ -44,9 +56,12 @@ static void upload(amg_handle* h, const HostCsr& H, DevCsr& D) {
     D.nrows = (int32_t)H.nrows;
     D.ncols = (int32_t)H.ncols;
     D.nnz = H.nnz();
-    D.ptr = halloc<int32_t>(h, H.nrows + 1);
-    D.col = halloc<int32_t>(h, D.nnz);
-    D.val = halloc<double>(h, D.nnz);
+    D.ptr = halloc<int32_t>(h, H.nrows + 1 + kPad);
+    D.col = halloc<int32_t>(h, D.nnz + kPad);
+    D.val = halloc<double>(h, D.nnz + kPad);
+    AMG_CUDA(cudaMemset(D.ptr, 0, (H.nrows + 1 + kPad) * sizeof(int32_t)));
+    AMG_CUDA(cudaMemset(D.col, 0, (D.nnz + kPad) * sizeof(int32_t)));
+    AMG_CUDA(cudaMemset(D.val, 0, (D.nnz + kPad) * sizeof(double)));
     AMG_CUDA(cudaMemcpy(D.ptr, H.ptr.data(), (H.nrows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     AMG_CUDA(cudaMemcpy(D.col, H.col.data(), D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
     AMG_CUDA(cudaMemcpy(D.val, H.val.data(), D.nnz * sizeof(double), cudaMemcpyHostToDevice));
@@ -438,6 +453,7 @@ static CachedGraph capture(amg_handle* h, const double* f, double* x) {
         issue_post(h, I3, f, x, b);
         g.post_launches = I3.launches;
         AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, cs));
+        enqueue_dev_err_copy(h->err_host, cs);
         capturing = false;
         AMG_CUDA(cudaStreamEndCapture(cs, &g.graph));
         AMG_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
@@ -504,6 +520,7 @@ static int64_t attempt(amg_handle* h, const double* f, double* x, bool use_graph
     }
     issue_post(h, I, f, x, b);
     AMG_CUDA(cudaMemcpyAsync(h->st_out, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->stream));
+    enqueue_dev_err_copy(h->err_host, h->stream);
     AMG_CUDA(cudaStreamSynchronize(h->stream));
     return I.launches - l0;
 }
@@ -520,7 +537,12 @@ amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int
     int64_t launches = 0;
     amg_status status = AMG_OK;
     for (int attempt_no = 0; attempt_no < 64; ++attempt_no) {
+        *h->err_host = 0;
         launches += attempt(h, f, x, use_graph && !h->graph_unsupported, prof);
+        if (*h->err_host) {
+            read_and_clear_dev_err();
+            fail(AMG_ERR_CUDA, "a device pipeline wait timed out; results are invalid");
+        }
         const KState& o = *h->st_out;
         if (o.zero_rhs) {
             AMG_CUDA(cudaMemsetAsync(x, 0, h->n * sizeof(double), h->stream));

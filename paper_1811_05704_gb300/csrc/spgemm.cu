@@ -272,7 +272,8 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     int* err = dev_alloc<int>(1);
     AMG_CUDA(cudaMemsetAsync(nbig, 0, sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    C.ptr = dev_alloc<int32_t>(m + 1);
+    C.ptr = dev_alloc<int32_t>(m + 1 + kPad);
+    AMG_CUDA(cudaMemsetAsync(C.ptr, 0, (m + 1 + kPad) * sizeof(int32_t), s));
 
     const unsigned wgrid = (unsigned)((m + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (m > 0) {
@@ -309,8 +310,10 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
         fail(AMG_ERR_TOO_LARGE, "Galerkin product row wider than 4096 columns");
     }
     C.nnz = nnz;
-    C.col = dev_alloc<int32_t>(nnz > 0 ? nnz : 1);
-    C.val = dev_alloc<double>(nnz > 0 ? nnz : 1);
+    C.col = dev_alloc<int32_t>(nnz + kPad);
+    C.val = dev_alloc<double>(nnz + kPad);
+    AMG_CUDA(cudaMemsetAsync(C.col, 0, (nnz + kPad) * sizeof(int32_t), s));
+    AMG_CUDA(cudaMemsetAsync(C.val, 0, (nnz + kPad) * sizeof(double), s));
     if (m > 0) {
         AMG_CUDA(cudaFuncSetAttribute(k_num_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)num_warp_smem));

@@ -21,177 +21,192 @@
 
 #include "amg_internal.h"
 #include "device_common.cuh"
+#include "epilogues.cuh"
 
 namespace amg {
 
-// ------------------------------------------------------------ epilogues
-// Each epilogue provides: acc_t, ndot (dot products it contributes), xg(c)
-// (the gathered operand for column c) and store(r, s, d0, d1).
-struct EpiY {
-    using acc_t = double;
-    static constexpr int ndot = 0;
-    const double* __restrict__ x;
-    double* __restrict__ y;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, double s, double&, double&) const { y[r] = s; }
+// ---------------------------------------------------- streaming engine
+// Persistent, warp-specialised CSR kernel.  The matrix is split into tiles
+// (consecutive rows, at most kTileNnz nonzeros and kRowsPerBlock rows); CTA b
+// owns a contiguous run of tiles.  One producer lane streams each tile's row
+// pointers, column indices and values into a kStages-deep shared-memory ring
+// with bulk asynchronous copies (cp.async.bulk, completion counted on an
+// mbarrier, evict-first in L2 so that the gathered vectors stay resident);
+// eight consumer warps take `vw` lanes per row, gather the operand through
+// L2, reduce the row with shuffles and run the epilogue.  With programmatic
+// dependent launch the producer fetches its first tiles -- constant matrix
+// data -- before waiting for the previous kernel, so consecutive kernels of
+// the solve overlap their pipeline fill with the predecessor's tail.
+constexpr int kCons = 256;      // consumer threads per CTA
+constexpr int kStages = 3;
+constexpr int kCtasPerSm = 2;
+
+__device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
+
+template <typename VT>
+struct StreamLayout {
+    static constexpr int rp_n = kRowsPerBlock + 8;
+    static constexpr int nz_n = kTileNnz + 8;
+    static constexpr size_t stage = (size_t)rp_n * 4 + (size_t)nz_n * 4 + (size_t)nz_n * sizeof(VT);
+    static constexpr size_t header = 128;
+    static constexpr size_t total = header + kStages * stage;
 };
 
-struct EpiYDot {  // y = A x, dot w.y
-    using acc_t = double;
-    static constexpr int ndot = 1;
-    const double* __restrict__ x;
-    const double* __restrict__ w;
-    double* __restrict__ y;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, double s, double& d0, double&) const {
-        y[r] = s;
-        d0 = __ldg(w + r) * s;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (seconds), records bit 2 in
+// g_dev_err and returns false instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+        if (mbar_try(b, parity)) return true;
+    atomicOr(&g_dev_err, 4);
+    return false;
+}
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// bulk global -> shared copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename VT, typename Epi>
+__global__ void __launch_bounds__(kCons + 32, kCtasPerSm)
+k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+         const VT* __restrict__ val, const int2* __restrict__ tiles, int ntiles, int vw, Epi epi,
+         Reduce red, const int* __restrict__ skip) {
+    using acc_t = typename Epi::acc_t;
+    using L = StreamLayout<VT>;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm);
+    uint64_t* empty = full + kStages;
+    int4* info = reinterpret_cast<int4*>(sm + 64);
+    auto rp_of = [&](int s) { return reinterpret_cast<int*>(sm + L::header + s * L::stage); };
+    auto col_of = [&](int s) { return rp_of(s) + L::rp_n; };
+    auto val_of = [&](int s) { return reinterpret_cast<VT*>(col_of(s) + L::nz_n); };
+
+    const int tid = threadIdx.x;
+    const int t0 = (int)((long long)ntiles * blockIdx.x / gridDim.x);
+    const int t1 = (int)((long long)ntiles * (blockIdx.x + 1) / gridDim.x);
+    const int count = t1 - t0;
+    const int first = min(kStages, count);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCons / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-};
+    __syncthreads();
+    pdl_trigger();
 
-struct EpiRes0 {  // t = f - A x
-    using acc_t = double;
-    static constexpr int ndot = 0;
-    const double* __restrict__ f;
-    const double* __restrict__ x;
-    double* __restrict__ t;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, double s, double&, double&) const { t[r] = __ldg(f + r) - s; }
-};
-
-struct EpiYDot2 {  // y = A x, dots y.y and y.w
-    using acc_t = double;
-    static constexpr int ndot = 2;
-    const double* __restrict__ x;
-    const double* __restrict__ w;
-    double* __restrict__ y;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, double s, double& d0, double& d1) const {
-        y[r] = s;
-        d0 = s * s;
-        d1 = s * __ldg(w + r);
+    double d0 = 0.0, d1 = 0.0;
+    bool stop = false;  // set by an earlier kernel; the same value in every block of the grid
+    if (tid >= kCons) {
+        if (tid != kCons) {
+            pdl_wait();
+            stop = skip && *(volatile const int*)skip;
+        } else {  // producer lane
+            const uint64_t pol = evict_first_policy();
+            auto issue = [&](int i) {
+                const int s = i % kStages;
+                const int2 a = tiles[t0 + i], b = tiles[t0 + i + 1];
+                const int ar = a.x & ~3, re = (b.x + 1 + 3) & ~3;
+                const int ak = a.y & ~3, ke = (b.y + 3) & ~3;
+                info[s] = make_int4(a.x, b.x, ar, ak);
+                const uint32_t brp = (uint32_t)(re - ar) * 4u;
+                const uint32_t bnz = (uint32_t)(ke - ak);
+                mbar_arrive_tx(&full[s], brp + bnz * (4u + (uint32_t)sizeof(VT)));
+                bulk_g2s(rp_of(s), ptr + ar, brp, &full[s], pol);
+                if (bnz) {
+                    bulk_g2s(col_of(s), col + ak, bnz * 4u, &full[s], pol);
+                    bulk_g2s(val_of(s), val + ak, bnz * (uint32_t)sizeof(VT), &full[s], pol);
+                }
+            };
+            for (int i = 0; i < first; ++i) issue(i);
+            pdl_wait();
+            stop = skip && *(volatile const int*)skip;
+            if (!stop)
+                for (int i = first; i < count; ++i) {
+                    if (!mbar_wait(&empty[i % kStages], ((i / kStages) - 1) & 1)) break;
+                    issue(i);
+                }
+        }
+    } else {
+        pdl_wait();
+        stop = skip && *(volatile const int*)skip;
+        const int n = stop ? first : count;
+        const int grp = tid / vw, lane = tid - grp * vw;
+        for (int i = 0; i < n; ++i) {
+            const int s = i % kStages;
+            if (!mbar_wait(&full[s], (i / kStages) & 1)) break;
+            if (!stop) {
+                const int4 inf = info[s];
+                const int* rp = rp_of(s);
+                const int* cs = col_of(s);
+                const VT* vs = val_of(s);
+                const int row = inf.x + grp;
+                const bool active = row < inf.y;
+                typename Epi::Pre pre{};
+                if (active && lane == 0) pre = epi.load(row);
+                acc_t sum = acc_t(0);
+                if (active) {
+                    const int kb = rp[row - inf.z] - inf.w, ke = rp[row + 1 - inf.z] - inf.w;
+#pragma unroll 4
+                    for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
+                }
+                for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
+                if (active && lane == 0) {
+                    double e0 = 0.0, e1 = 0.0;
+                    epi.store(row, sum, pre, e0, e1);
+                    d0 += e0;
+                    d1 += e1;
+                }
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+        }
     }
-};
-
-struct EpiPre {  // x = d f ; t = f - A x   (first pre-sweep from zero + residual)
-    using acc_t = double;
-    static constexpr int ndot = 0;
-    const double* __restrict__ d;
-    const double* __restrict__ f;
-    double* __restrict__ x;
-    double* __restrict__ t;
-    __device__ double xg(int c) const { return __ldg(d + c) * __ldg(f + c); }
-    __device__ void store(int r, double s, double&, double&) const {
-        const double fr = __ldg(f + r);
-        x[r] = __ldg(d + r) * fr;
-        t[r] = fr - s;
+    if constexpr (Epi::ndot > 0) {
+        if (!stop) reduce_finalize(red, d0, d1);  // a skipped kernel contributes no dot products
     }
-};
+}
 
-template <bool DOT>
-struct EpiSmooth {  // y = x + d (f - A x) ; optional w.y
-    using acc_t = double;
-    static constexpr int ndot = DOT ? 1 : 0;
-    const double* __restrict__ d;
-    const double* __restrict__ f;
-    const double* __restrict__ x;
-    double* __restrict__ y;
-    const double* __restrict__ w;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, double s, double& d0, double&) const {
-        const double v = __ldg(x + r) + __ldg(d + r) * (__ldg(f + r) - s);
-        y[r] = v;
-        if (DOT) d0 = __ldg(w + r) * v;
-    }
-};
-
-struct EpiResid {  // r = f - A x (optionally also into r2), dots r.r and f.f
-    using acc_t = double;
-    static constexpr int ndot = 2;
-    const double* __restrict__ f;
-    const double* __restrict__ x;
-    double* __restrict__ r;
-    double* __restrict__ r2;
-    __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int i, double s, double& d0, double& d1) const {
-        const double fi = __ldg(f + i);
-        const double v = fi - s;
-        r[i] = v;
-        if (r2) r2[i] = v;
-        d0 = v * v;
-        d1 = fi * fi;
-    }
-};
-
-struct EpiProlong {  // x += P xc
-    using acc_t = double;
-    static constexpr int ndot = 0;
-    const double* __restrict__ xc;
-    double* __restrict__ x;
-    __device__ double xg(int c) const { return __ldg(xc + c); }
-    __device__ void store(int r, double s, double&, double&) const { x[r] += s; }
-};
-
-// float32 V-cycle epilogues: level vectors in float32; on the finest level the
-// right-hand side (the Krylov vector) is read in float64 and the output is
-// written in float64.
-struct EpiY32 {
-    using acc_t = float;
-    static constexpr int ndot = 0;
-    const float* __restrict__ x;
-    float* __restrict__ y;
-    __device__ float xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, float s, double&, double&) const { y[r] = s; }
-};
-
-struct EpiPre32 {
-    using acc_t = float;
-    static constexpr int ndot = 0;
-    const float* __restrict__ d;
-    const float* __restrict__ f32;   // level rhs (levels >= 1)
-    const double* __restrict__ f64;  // finest-level rhs (Krylov vector), or null
-    float* __restrict__ x;
-    float* __restrict__ t;
-    __device__ float fv(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
-    __device__ float xg(int c) const { return __ldg(d + c) * fv(c); }
-    __device__ void store(int r, float s, double&, double&) const {
-        const float fr = fv(r);
-        x[r] = __ldg(d + r) * fr;
-        t[r] = fr - s;
-    }
-};
-
-template <bool DOT>
-struct EpiSmooth32 {
-    using acc_t = float;
-    static constexpr int ndot = DOT ? 1 : 0;
-    const float* __restrict__ d;
-    const float* __restrict__ f32;
-    const double* __restrict__ f64;
-    const float* __restrict__ x;
-    float* __restrict__ y32;   // level output (levels >= 1)
-    double* __restrict__ y64;  // finest-level output, or null
-    const double* __restrict__ w;
-    __device__ float fv(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
-    __device__ float xg(int c) const { return __ldg(x + c); }
-    __device__ void store(int r, float s, double& d0, double&) const {
-        const float v = __ldg(x + r) + __ldg(d + r) * (fv(r) - s);
-        if (y64) y64[r] = (double)v;
-        else y32[r] = v;
-        if (DOT) d0 = __ldg(w + r) * (double)v;
-    }
-};
-
-struct EpiProlong32 {
-    using acc_t = float;
-    static constexpr int ndot = 0;
-    const float* __restrict__ xc;
-    float* __restrict__ x;
-    __device__ float xg(int c) const { return __ldg(xc + c); }
-    __device__ void store(int r, float s, double&, double&) const { x[r] += s; }
-};
-
-// -------------------------------------------------------------- engine
+// ------------------------------------------------------ row-chunk engine
+// Fallback for matrices with a row longer than one tile, and the
+// bounds-checked standalone product: a block takes a run of rows, stages the
+// products of kTileNnz nonzeros at a time in shared memory and reduces each
+// row in column order (a thread per row, or a warp per row for long rows).
 template <typename VT>
 __device__ __forceinline__ VT ld_stream(const VT* p) { return __ldcs(p); }
 
@@ -222,11 +237,12 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     __syncthreads();
     const int k0 = rp[0], k1 = rp[nr];
     const bool warp_rows = (k1 - k0) >= 24 * nr;  // long rows: a warp per row
+    typename Epi::Pre pre{};
+    if (tid < nr) pre = epi.load(r0 + tid);
 
     acc_t acc = acc_t(0);
     for (int c0 = k0; c0 < k1; c0 += kTileNnz) {
         const int c1 = min(c0 + kTileNnz, k1);
-        // gather: products of this tile into shared memory, 4 loads in flight
         for (int base = c0 + tid; base < c1; base += 4 * kThreads) {
             int cc[4];
             VT vv[4];
@@ -273,14 +289,63 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     if (warp_rows) acc = (tid < nr) ? rowsum[tid] : acc_t(0);
 
     double d0 = 0.0, d1 = 0.0;
-    if (tid < nr) epi.store(r0 + tid, acc, d0, d1);
+    if (tid < nr) epi.store(r0 + tid, acc, pre, d0, d1);
     if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
+}
+
+static int g_sm_count = 0;
+static bool g_pdl = true;
+
+void set_stream_options(bool pdl) { g_pdl = pdl; }
+
+int stream_grid(int ntiles) {
+    if (g_sm_count == 0) {
+        int dev = 0;
+        AMG_CUDA(cudaGetDevice(&dev));
+        AMG_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return std::max(1, std::min(ntiles, kCtasPerSm * g_sm_count));
+}
+
+void enqueue_dev_err_copy(int* host_dst, cudaStream_t s) {
+    AMG_CUDA(cudaMemcpyFromSymbolAsync(host_dst, g_dev_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+}
+
+int read_and_clear_dev_err() {
+    int v = 0, z = 0;
+    AMG_CUDA(cudaMemcpyFromSymbol(&v, g_dev_err, sizeof(int)));
+    if (v) AMG_CUDA(cudaMemcpyToSymbol(g_dev_err, &z, sizeof(int)));
+    return v;
 }
 
 template <typename VT, typename Epi>
 static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
                 const int* skip, cudaStream_t s) {
     if (A.nrows == 0) return;
+    if (A.tiles) {
+        const int grid = stream_grid(A.ntiles);
+        if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
+        static bool configured = false;  // per template instance
+        const size_t smem = StreamLayout<VT>::total;
+        if (!configured) {
+            AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            configured = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kCons + 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = g_pdl ? 1 : 0;
+        AMG_CUDA(cudaLaunchKernelEx(&cfg, k_stream<VT, Epi>, (const int32_t*)A.ptr, (const int32_t*)A.col,
+                                    val, (const int2*)A.tiles, (int)A.ntiles, (int)A.vw, epi, red, skip));
+        return;
+    }
     if (Epi::ndot > 0 && A.nblk > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
     k_spmv<VT, Epi, false><<<A.nblk, kThreads, 0, s>>>(A.ptr, A.col, val, A.blk, A.nrows, A.ncols,
                                                         0, epi, red, skip, nullptr);
