@@ -48,7 +48,8 @@ void host_dense_inverse(const HostCsr& A, std::vector<double>& inv);  // row-maj
 std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_cap, int nnz_cap);
 // streaming-engine tiles: (row, nonzero) boundaries and lanes per row; empty
 // if a row has more than nnz_cap nonzeros
-std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int& vw);
+std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int rows_cap_max,
+                                int& vw, int& rows_cap);
 
 // ---------------------------------------------------------- device CSR
 // Row-block schedule: block b of the SpMV kernel covers rows
@@ -70,6 +71,9 @@ struct DevCsr {
     int2* tiles = nullptr;   // streaming-engine tiles {first row, first nonzero}, ntiles + 1
     int32_t ntiles = 0;      // 0: some row is longer than a tile, use the row-chunk engine
     int32_t vw = 1;          // lanes per row in the streaming engine
+    int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R)
+    double* vald = nullptr;  // a_ij d_j: values scaled by the smoother diagonal (level A only)
+    float* vald32 = nullptr;
 };
 // Device CSR arrays carry kPad readable elements past their end (row_ptr
 // past n + 1, col/val past nnz): the streaming engine copies 16-byte-aligned

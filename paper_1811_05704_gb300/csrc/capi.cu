@@ -172,9 +172,10 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             AMG_CUDA(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
             AMG_CUDA(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
             build_hierarchy(h, std::move(H));
-            auto vec = [&](double*& v) {
-                v = dev_alloc<double>(h->n);
+            auto vec = [&](double*& v) {  // padded: see kPad
+                v = dev_alloc<double>(h->n + kPad);
                 h->dev_allocs.push_back(v);
+                AMG_CUDA(cudaMemset(v, 0, (h->n + kPad) * sizeof(double)));
             };
             for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->rh, &h->v, &h->ph, &h->sv, &h->sh,
                                &h->tv, &h->fbuf, &h->xbuf})

@@ -1,10 +1,15 @@
 // epilogues.cuh -- what each step of the solve does around one sparse row
 // product s_i = sum_j a_ij g(x_j).  An epilogue provides
-//   acc_t         accumulation type
-//   ndot          number of dot products it contributes (0..2)
-//   xg(c)         the gathered operand g for column c
-//   Pre load(i)   row-indexed inputs of row i (loaded before the row product,
-//                 so their latency overlaps the gathers)
+//   acc_t             accumulation type
+//   ndot              number of dot products it contributes (0..2)
+//   nvec, vptr(k), vbytes(k)
+//                     row-indexed input vectors (internal, padded buffers)
+//                     that the streaming engine copies into shared memory with
+//                     the tile; an epilogue that reads caller memory by row
+//                     (the residual of the initial guess) lists none and
+//                     loads it directly
+//   xg(c)             the gathered operand g for column c
+//   Pre load(i, vt)   row-indexed inputs of row i (from the tile's copies)
 //   store(i, s, pre, d0, d1)   write the outputs of row i, set dot terms
 #pragma once
 
@@ -12,28 +17,44 @@
 
 namespace amg {
 
+// Row-indexed vector slices of one tile: vector k, row i lives at
+// base[k] + (i - row0) * elem.  For the row-chunk engine base[k] is the
+// global vector itself and row0 = 0.
+struct VecTile {
+    const unsigned char* base[4];
+    int row0;
+    template <typename T>
+    __device__ __forceinline__ T at(int k, int i) const {
+        return reinterpret_cast<const T*>(base[k])[i - row0];
+    }
+};
+
 struct Empty {};
 
 struct EpiY {  // y = A x
     using acc_t = double;
     using Pre = Empty;
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 0;
     const double* __restrict__ x;
     double* __restrict__ y;
+    __device__ const void* vptr(int) const { return nullptr; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int) const { return {}; }
+    __device__ Pre load(int, const VecTile&) const { return {}; }
     __device__ void store(int r, double s, const Pre&, double&, double&) const { y[r] = s; }
 };
 
 struct EpiYDot {  // y = A x, dot w.y
     using acc_t = double;
     struct Pre { double w; };
-    static constexpr int ndot = 1;
+    static constexpr int ndot = 1, nvec = 1;
     const double* __restrict__ x;
     const double* __restrict__ w;
     double* __restrict__ y;
+    __device__ const void* vptr(int) const { return w; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int r) const { return {__ldg(w + r)}; }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double& d0, double&) const {
         y[r] = s;
         d0 = p.w * s;
@@ -43,12 +64,14 @@ struct EpiYDot {  // y = A x, dot w.y
 struct EpiYDot2 {  // y = A x, dots y.y and y.w
     using acc_t = double;
     struct Pre { double w; };
-    static constexpr int ndot = 2;
+    static constexpr int ndot = 2, nvec = 1;
     const double* __restrict__ x;
     const double* __restrict__ w;
     double* __restrict__ y;
+    __device__ const void* vptr(int) const { return w; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int r) const { return {__ldg(w + r)}; }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double& d0, double& d1) const {
         y[r] = s;
         d0 = s * s;
@@ -59,25 +82,32 @@ struct EpiYDot2 {  // y = A x, dots y.y and y.w
 struct EpiRes0 {  // t = f - A x
     using acc_t = double;
     struct Pre { double f; };
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 1;
     const double* __restrict__ f;
     const double* __restrict__ x;
     double* __restrict__ t;
+    __device__ const void* vptr(int) const { return f; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int r) const { return {__ldg(f + r)}; }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double&, double&) const { t[r] = p.f - s; }
 };
 
-struct EpiPre {  // x = d f ; t = f - A x   (first pre-sweep from zero, then the residual)
+// x = d f ; t = f - A x, the first pre-sweep from zero and the residual.  The
+// matrix passed with this epilogue holds a_ij d_j (values scaled by the
+// smoother diagonal at setup), so that A (d f) needs one gather, of f.
+struct EpiPre {
     using acc_t = double;
     struct Pre { double d, f; };
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 2;
     const double* __restrict__ d;
     const double* __restrict__ f;
     double* __restrict__ x;
     double* __restrict__ t;
-    __device__ double xg(int c) const { return __ldg(d + c) * __ldg(f + c); }
-    __device__ Pre load(int r) const { return {__ldg(d + r), __ldg(f + r)}; }
+    __device__ const void* vptr(int k) const { return k == 0 ? (const void*)d : (const void*)f; }
+    __device__ int vbytes(int) const { return 8; }
+    __device__ double xg(int c) const { return __ldg(f + c); }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r), v.at<double>(1, r)}; }
     __device__ void store(int r, double s, const Pre& p, double&, double&) const {
         x[r] = p.d * p.f;
         t[r] = p.f - s;
@@ -88,33 +118,66 @@ template <bool DOT>
 struct EpiSmooth {  // y = x + d (f - A x) ; optional w.y
     using acc_t = double;
     struct Pre { double x, d, f, w; };
-    static constexpr int ndot = DOT ? 1 : 0;
+    static constexpr int ndot = DOT ? 1 : 0, nvec = DOT ? 4 : 3;
     const double* __restrict__ d;
     const double* __restrict__ f;
     const double* __restrict__ x;
     double* __restrict__ y;
     const double* __restrict__ w;
+    __device__ const void* vptr(int k) const {
+        return k == 0 ? (const void*)x : k == 1 ? (const void*)d : k == 2 ? (const void*)f : (const void*)w;
+    }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int r) const {
-        return {__ldg(x + r), __ldg(d + r), __ldg(f + r), DOT ? __ldg(w + r) : 0.0};
+    __device__ Pre load(int r, const VecTile& v) const {
+        return {v.at<double>(0, r), v.at<double>(1, r), v.at<double>(2, r), DOT ? v.at<double>(3, r) : 0.0};
     }
     __device__ void store(int r, double s, const Pre& p, double& d0, double&) const {
-        const double v = p.x + p.d * (p.f - s);
-        y[r] = v;
-        if (DOT) d0 = p.w * v;
+        const double val = p.x + p.d * (p.f - s);
+        y[r] = val;
+        if (DOT) d0 = p.w * val;
     }
 };
 
-struct EpiResid {  // r = f - A x (optionally also into r2), dots r.r and f.f
+// y = x + d (f - A x) and f.y: the finest-level post-sweep, whose right-hand
+// side is the Krylov residual that the dot product pairs with.
+struct EpiSmoothDotF {
+    using acc_t = double;
+    struct Pre { double x, d, f; };
+    static constexpr int ndot = 1, nvec = 3;
+    const double* __restrict__ d;
+    const double* __restrict__ f;
+    const double* __restrict__ x;
+    double* __restrict__ y;
+    __device__ const void* vptr(int k) const {
+        return k == 0 ? (const void*)x : k == 1 ? (const void*)d : (const void*)f;
+    }
+    __device__ int vbytes(int) const { return 8; }
+    __device__ double xg(int c) const { return __ldg(x + c); }
+    __device__ Pre load(int r, const VecTile& v) const {
+        return {v.at<double>(0, r), v.at<double>(1, r), v.at<double>(2, r)};
+    }
+    __device__ void store(int r, double s, const Pre& p, double& d0, double&) const {
+        const double val = p.x + p.d * (p.f - s);
+        y[r] = val;
+        d0 = p.f * val;
+    }
+};
+
+// r = f - A x (optionally also into r2), dots r.r and f.f.  f and x may be the
+// caller's buffers, so f is read directly (no shared-memory copy).
+struct EpiResid {
     using acc_t = double;
     struct Pre { double f; };
-    static constexpr int ndot = 2;
+    static constexpr int ndot = 2, nvec = 0;
     const double* __restrict__ f;
     const double* __restrict__ x;
     double* __restrict__ r;
     double* __restrict__ r2;
+    __device__ const void* vptr(int) const { return nullptr; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int i) const { return {__ldg(f + i)}; }
+    __device__ Pre load(int i, const VecTile&) const { return {__ldg(f + i)}; }
     __device__ void store(int i, double s, const Pre& p, double& d0, double& d1) const {
         const double v = p.f - s;
         r[i] = v;
@@ -127,11 +190,13 @@ struct EpiResid {  // r = f - A x (optionally also into r2), dots r.r and f.f
 struct EpiProlong {  // x += P xc
     using acc_t = double;
     struct Pre { double x; };
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 1;
     const double* __restrict__ xc;
     double* __restrict__ x;
+    __device__ const void* vptr(int) const { return x; }
+    __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(xc + c); }
-    __device__ Pre load(int r) const { return {x[r]}; }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double&, double&) const { x[r] = p.x + s; }
 };
 
@@ -141,26 +206,33 @@ struct EpiProlong {  // x += P xc
 struct EpiY32 {
     using acc_t = float;
     using Pre = Empty;
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 0;
     const float* __restrict__ x;
     float* __restrict__ y;
+    __device__ const void* vptr(int) const { return nullptr; }
+    __device__ int vbytes(int) const { return 4; }
     __device__ float xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int) const { return {}; }
+    __device__ Pre load(int, const VecTile&) const { return {}; }
     __device__ void store(int r, float s, const Pre&, double&, double&) const { y[r] = s; }
 };
 
-struct EpiPre32 {
+struct EpiPre32 {  // as EpiPre, with matrix values a_ij d_j in float32
     using acc_t = float;
     struct Pre { float d, f; };
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 2;
     const float* __restrict__ d;
     const float* __restrict__ f32;   // level rhs (levels >= 1)
     const double* __restrict__ f64;  // finest-level rhs, or null
     float* __restrict__ x;
     float* __restrict__ t;
-    __device__ float fv(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
-    __device__ float xg(int c) const { return __ldg(d + c) * fv(c); }
-    __device__ Pre load(int r) const { return {__ldg(d + r), fv(r)}; }
+    __device__ const void* vptr(int k) const {
+        return k == 0 ? (const void*)d : (f64 ? (const void*)f64 : (const void*)f32);
+    }
+    __device__ int vbytes(int k) const { return (k == 1 && f64) ? 8 : 4; }
+    __device__ float xg(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
+    __device__ Pre load(int r, const VecTile& v) const {
+        return {v.at<float>(0, r), f64 ? (float)v.at<double>(1, r) : v.at<float>(1, r)};
+    }
     __device__ void store(int r, float s, const Pre& p, double&, double&) const {
         x[r] = p.d * p.f;
         t[r] = p.f - s;
@@ -171,7 +243,7 @@ template <bool DOT>
 struct EpiSmooth32 {
     using acc_t = float;
     struct Pre { float x, d, f; double w; };
-    static constexpr int ndot = DOT ? 1 : 0;
+    static constexpr int ndot = DOT ? 1 : 0, nvec = DOT ? 4 : 3;
     const float* __restrict__ d;
     const float* __restrict__ f32;
     const double* __restrict__ f64;
@@ -179,27 +251,36 @@ struct EpiSmooth32 {
     float* __restrict__ y32;   // level output (levels >= 1)
     double* __restrict__ y64;  // finest-level output, or null
     const double* __restrict__ w;
-    __device__ float fv(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
+    __device__ const void* vptr(int k) const {
+        return k == 0 ? (const void*)x
+             : k == 1 ? (const void*)d
+             : k == 2 ? (f64 ? (const void*)f64 : (const void*)f32)
+                      : (const void*)w;
+    }
+    __device__ int vbytes(int k) const { return (k == 3 || (k == 2 && f64)) ? 8 : 4; }
     __device__ float xg(int c) const { return __ldg(x + c); }
-    __device__ Pre load(int r) const {
-        return {__ldg(x + r), __ldg(d + r), fv(r), DOT ? __ldg(w + r) : 0.0};
+    __device__ Pre load(int r, const VecTile& v) const {
+        return {v.at<float>(0, r), v.at<float>(1, r),
+                f64 ? (float)v.at<double>(2, r) : v.at<float>(2, r), DOT ? v.at<double>(3, r) : 0.0};
     }
     __device__ void store(int r, float s, const Pre& p, double& d0, double&) const {
-        const float v = p.x + p.d * (p.f - s);
-        if (y64) y64[r] = (double)v;
-        else y32[r] = v;
-        if (DOT) d0 = p.w * (double)v;
+        const float val = p.x + p.d * (p.f - s);
+        if (y64) y64[r] = (double)val;
+        else y32[r] = val;
+        if (DOT) d0 = p.w * (double)val;
     }
 };
 
 struct EpiProlong32 {
     using acc_t = float;
     struct Pre { float x; };
-    static constexpr int ndot = 0;
+    static constexpr int ndot = 0, nvec = 1;
     const float* __restrict__ xc;
     float* __restrict__ x;
+    __device__ const void* vptr(int) const { return x; }
+    __device__ int vbytes(int) const { return 4; }
     __device__ float xg(int c) const { return __ldg(xc + c); }
-    __device__ Pre load(int r) const { return {x[r]}; }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<float>(0, r)}; }
     __device__ void store(int r, float s, const Pre& p, double&, double&) const { x[r] = p.x + s; }
 };
 

@@ -294,10 +294,12 @@ std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_c
 
 // Tiles of the streaming engine: `vw` lanes share a row (a power of two
 // about a sixth of the mean row length, so each lane handles a handful of
-// nonzeros), at most kRowsPerBlock / vw rows and nnz_cap nonzeros per tile.
-// Returned as flattened (first row, first nonzero) pairs, one per tile plus
-// the end; empty if a single row exceeds nnz_cap.
-std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int& vw) {
+// nonzeros); a tile holds at most nnz_cap nonzeros and rows_cap rows, where
+// rows_cap is one consumer pass (256/vw rows), or two passes when the rows are
+// short enough for two passes to fit in nnz_cap, capped by rows_cap_max.  Returned as flattened (first row, first nonzero) pairs,
+// one per tile plus the end; empty if a single row exceeds nnz_cap.
+std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int rows_cap_max,
+                                int& vw, int& rows_cap) {
     const int64_t n = (int64_t)ptr.size() - 1;
     int64_t longest = 0;
     for (int64_t i = 0; i < n; ++i) longest = std::max<int64_t>(longest, ptr[i + 1] - ptr[i]);
@@ -305,7 +307,10 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
     const double avg = (double)ptr[n] / (double)n;
     vw = 1;
     while (vw < 32 && 2.0 * vw <= avg / 6.0) vw *= 2;
-    const std::vector<int32_t> rows = host_row_blocks(ptr, kRowsPerBlock / vw, nnz_cap);
+    // a second consumer pass only when two passes of rows still fit the tile
+    const int pass = kRowsPerBlock / vw;
+    rows_cap = (2.0 * pass * avg <= (double)nnz_cap) ? std::min(rows_cap_max, 2 * pass) : pass;
+    const std::vector<int32_t> rows = host_row_blocks(ptr, rows_cap, nnz_cap);
     std::vector<int32_t> out;
     out.reserve(2 * rows.size());
     for (int32_t r : rows) {

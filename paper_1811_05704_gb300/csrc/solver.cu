@@ -28,18 +28,19 @@ static void track(amg_handle* h, const DevCsr& D) {
     h->dev_allocs.push_back(D.val);
 }
 
-static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D) {
+static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, int rows_cap_max) {
     const std::vector<int32_t> blk = host_row_blocks(ptr, kRowsPerBlock, kTileNnz);
     D.nblk = (int32_t)blk.size() - 1;
     D.blk = halloc<int32_t>(h, blk.size());
     AMG_CUDA(cudaMemcpy(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    int vw = 1;
-    const std::vector<int32_t> tiles = host_tiles(ptr, kTileNnz, vw);
+    int vw = 1, rows_cap = kRowsPerBlock;
+    const std::vector<int32_t> tiles = host_tiles(ptr, kTileNnz, rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
     D.ntiles = 0;
     if (!tiles.empty() && h->prm.use_stream) {
         D.ntiles = (int32_t)tiles.size() / 2 - 1;
         D.vw = vw;
+        D.rows_cap = rows_cap;
         int32_t* t = halloc<int32_t>(h, tiles.size());
         AMG_CUDA(cudaMemcpy(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         D.tiles = reinterpret_cast<int2*>(t);
@@ -52,7 +53,7 @@ static void make_f32(amg_handle* h, DevCsr& D) {
     launch_copy_to_f32(D.val, D.val32, D.nnz, h->stream);
 }
 
-static void upload(amg_handle* h, const HostCsr& H, DevCsr& D) {
+static void upload(amg_handle* h, const HostCsr& H, DevCsr& D, int rows_cap_max) {
     D.nrows = (int32_t)H.nrows;
     D.ncols = (int32_t)H.ncols;
     D.nnz = H.nnz();
@@ -65,7 +66,7 @@ static void upload(amg_handle* h, const HostCsr& H, DevCsr& D) {
     AMG_CUDA(cudaMemcpy(D.ptr, H.ptr.data(), (H.nrows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     AMG_CUDA(cudaMemcpy(D.col, H.col.data(), D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
     AMG_CUDA(cudaMemcpy(D.val, H.val.data(), D.nnz * sizeof(double), cudaMemcpyHostToDevice));
-    schedule(h, H.ptr, D);
+    schedule(h, H.ptr, D, rows_cap_max);
 }
 
 static void download(const DevCsr& D, HostCsr& H) {
@@ -90,14 +91,22 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
     h->lev.clear();
     h->lev.reserve(AMG_MAX_LEVELS + 1);  // references to levels stay valid below
     h->lev.emplace_back();
-    upload(h, A, h->lev[0].A);
+    upload(h, A, h->lev[0].A, kRowsPerBlock);
     for (int l = 0;; ++l) {
         Level& L = h->lev[l];
         const int64_t n = A.nrows;
         const std::vector<double> dg = host_diagonal(A);
         host_smoother_diag(A, dg, prm, L.dhost);
-        L.d = halloc<double>(h, n);
+        L.d = halloc<double>(h, n + kPad);
+        AMG_CUDA(cudaMemset(L.d, 0, (n + kPad) * sizeof(double)));
         AMG_CUDA(cudaMemcpy(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        {   // values scaled by the smoother diagonal, for the fused first pre-sweep
+            std::vector<double> vd(A.nnz());
+            for (int64_t k = 0; k < A.nnz(); ++k) vd[k] = A.val[k] * L.dhost[A.col[k]];
+            L.A.vald = halloc<double>(h, A.nnz() + kPad);
+            AMG_CUDA(cudaMemset(L.A.vald, 0, (A.nnz() + kPad) * sizeof(double)));
+            AMG_CUDA(cudaMemcpy(L.A.vald, vd.data(), A.nnz() * sizeof(double), cudaMemcpyHostToDevice));
+        }
         bool coarsest = n <= prm.coarse_enough || l + 1 >= prm.max_levels || l + 1 >= AMG_MAX_LEVELS;
         if (!coarsest) {
             double eps = prm.strength_eps;
@@ -116,8 +125,8 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
                 HostCsr P, R;
                 host_prolongation(A, dg, eps, L.agg, L.nagg, P, L.omega_p);
                 host_transpose(P, R);
-                upload(h, P, L.P);
-                upload(h, R, L.R);
+                upload(h, P, L.P, 2 * kRowsPerBlock);
+                upload(h, R, L.R, 2 * kRowsPerBlock);
                 DevCsr AP, Ac;
                 device_spgemm(L.A, L.P, AP, h->stream);
                 try {
@@ -130,7 +139,7 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
                 track(h, Ac);
                 HostCsr next;
                 download(Ac, next);
-                schedule(h, next.ptr, Ac);
+                schedule(h, next.ptr, Ac, kRowsPerBlock);
                 if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
                 h->lev.emplace_back();
                 h->lev.back().A = Ac;
@@ -139,9 +148,13 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         }
         if (f32) {
             make_f32(h, L.A);
-            L.d32 = halloc<float>(h, n);
+            L.A.vald32 = halloc<float>(h, L.A.nnz + kPad);
+            AMG_CUDA(cudaMemset(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float)));
+            launch_copy_to_f32(L.A.vald, L.A.vald32, L.A.nnz, h->stream);
+            L.d32 = halloc<float>(h, n + kPad);
             std::vector<float> d32(L.dhost.begin(), L.dhost.end());
-            AMG_CUDA(cudaMemcpy(L.d32, d32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+            d32.resize(n + kPad, 0.0f);
+            AMG_CUDA(cudaMemcpy(L.d32, d32.data(), (n + kPad) * sizeof(float), cudaMemcpyHostToDevice));
         }
         if (coarsest) {
             if (n > prm.max_coarse_dense)
@@ -162,13 +175,18 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         const int64_t n = L.A.nrows;
         const bool last = l == nl - 1;
         if (nl == 1) break;
-        if (l > 0) L.f = halloc<double>(h, n);
-        L.x = halloc<double>(h, n);
-        if (!last) { L.y = halloc<double>(h, n); L.t = halloc<double>(h, n); }
+        // padded: the streaming kernels copy 16-byte-aligned row slices
+        auto v64 = [&]() { double* p = halloc<double>(h, n + kPad);
+                           AMG_CUDA(cudaMemset(p, 0, (n + kPad) * sizeof(double))); return p; };
+        auto v32 = [&]() { float* p = halloc<float>(h, n + kPad);
+                           AMG_CUDA(cudaMemset(p, 0, (n + kPad) * sizeof(float))); return p; };
+        if (l > 0) L.f = v64();
+        L.x = v64();
+        if (!last) { L.y = v64(); L.t = v64(); }
         if (f32) {
-            if (l > 0) L.f32 = halloc<float>(h, n);
-            L.x32 = halloc<float>(h, n);
-            if (!last) { L.y32 = halloc<float>(h, n); L.t32 = halloc<float>(h, n); }
+            if (l > 0) L.f32 = v32();
+            L.x32 = v32();
+            if (!last) { L.y32 = v32(); L.t32 = v32(); }
         }
     }
     AMG_CUDA(cudaStreamSynchronize(h->stream));
@@ -568,7 +586,9 @@ amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int
 void run_vcycle(amg_handle* h, const double* r, double* z) {
     Issue I;
     I.s = h->stream;
-    issue_vcycle(h, I, r, z, nullptr, nullptr);
+    // the V-cycle streams row slices of its input: take it from a padded buffer
+    AMG_CUDA(cudaMemcpyAsync(h->r, r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    issue_vcycle(h, I, h->r, z, nullptr, nullptr);
     AMG_CUDA(cudaStreamSynchronize(h->stream));
 }
 

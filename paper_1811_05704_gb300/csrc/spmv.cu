@@ -43,13 +43,20 @@ constexpr int kCtasPerSm = 2;
 
 __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 
-template <typename VT>
+template <typename VT, int RMAX, int NV>
 struct StreamLayout {
-    static constexpr int rp_n = kRowsPerBlock + 8;
-    static constexpr int nz_n = kTileNnz + 8;
-    static constexpr size_t stage = (size_t)rp_n * 4 + (size_t)nz_n * 4 + (size_t)nz_n * sizeof(VT);
+    static constexpr int rp_n = RMAX + 8;       // row pointers of the tile (+ alignment slack)
+    static constexpr int nz_n = kTileNnz + 8;   // nonzeros of the tile (+ alignment slack)
+    static constexpr int vec_n = RMAX + 8;      // row-indexed vector slice, 8-byte slots
+    static constexpr size_t rp_bytes = (size_t)rp_n * 4;
+    static constexpr size_t col_bytes = (size_t)nz_n * 4;
+    static constexpr size_t val_bytes = (size_t)nz_n * sizeof(VT);
+    static constexpr size_t vec_bytes = (size_t)vec_n * 8;
+    static constexpr size_t stage = rp_bytes + col_bytes + val_bytes + NV * vec_bytes;
     static constexpr size_t header = 128;
     static constexpr size_t total = header + kStages * stage;
+    static_assert(rp_bytes % 16 == 0 && col_bytes % 16 == 0 && val_bytes % 16 == 0 && vec_bytes % 16 == 0,
+                  "bulk-copy destinations must stay 16-byte aligned");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -97,23 +104,35 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <typename VT, typename Epi>
+template <typename VT, typename Epi, int RMAX>
 __global__ void __launch_bounds__(kCons + 32, kCtasPerSm)
 k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
          const VT* __restrict__ val, const int2* __restrict__ tiles, int ntiles, int vw, Epi epi,
          Reduce red, const int* __restrict__ skip) {
     using acc_t = typename Epi::acc_t;
-    using L = StreamLayout<VT>;
+    constexpr int NV = Epi::nvec;
+    using L = StreamLayout<VT, RMAX, NV>;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* empty = full + kStages;
     int4* info = reinterpret_cast<int4*>(sm + 64);
-    auto rp_of = [&](int s) { return reinterpret_cast<int*>(sm + L::header + s * L::stage); };
-    auto col_of = [&](int s) { return rp_of(s) + L::rp_n; };
-    auto val_of = [&](int s) { return reinterpret_cast<VT*>(col_of(s) + L::nz_n); };
+    auto stage_of = [&](int s) { return sm + L::header + s * L::stage; };
+    auto rp_of = [&](int s) { return reinterpret_cast<int*>(stage_of(s)); };
+    auto col_of = [&](int s) { return reinterpret_cast<int*>(stage_of(s) + L::rp_bytes); };
+    auto val_of = [&](int s) { return reinterpret_cast<VT*>(stage_of(s) + L::rp_bytes + L::col_bytes); };
+    auto vec_of = [&](int s, int k) {
+        return stage_of(s) + L::rp_bytes + L::col_bytes + L::val_bytes + k * L::vec_bytes;
+    };
 
     const int tid = threadIdx.x;
     const int t0 = (int)((long long)ntiles * blockIdx.x / gridDim.x);
@@ -138,35 +157,53 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
             stop = skip && *(volatile const int*)skip;
         } else {  // producer lane
             const uint64_t pol = evict_first_policy();
+            int2 cur = tiles[t0], nxt = tiles[t0 + 1];
+            // matrix arrays stream once (evict first); the row-indexed vectors
+            // are copied with the default policy
             auto issue = [&](int i) {
                 const int s = i % kStages;
-                const int2 a = tiles[t0 + i], b = tiles[t0 + i + 1];
-                const int ar = a.x & ~3, re = (b.x + 1 + 3) & ~3;
-                const int ak = a.y & ~3, ke = (b.y + 3) & ~3;
-                info[s] = make_int4(a.x, b.x, ar, ak);
+                const int ar = cur.x & ~3, re = (nxt.x + 1 + 3) & ~3, vre = (nxt.x + 3) & ~3;
+                const int ak = cur.y & ~3, ke = (nxt.y + 3) & ~3;
+                info[s] = make_int4(cur.x, nxt.x, ar, ak);
                 const uint32_t brp = (uint32_t)(re - ar) * 4u;
                 const uint32_t bnz = (uint32_t)(ke - ak);
-                mbar_arrive_tx(&full[s], brp + bnz * (4u + (uint32_t)sizeof(VT)));
+                uint32_t bytes = brp + bnz * (4u + (uint32_t)sizeof(VT));
+                for (int k = 0; k < NV; ++k) bytes += (uint32_t)(vre - ar) * (uint32_t)epi.vbytes(k);
+                mbar_arrive_tx(&full[s], bytes);
                 bulk_g2s(rp_of(s), ptr + ar, brp, &full[s], pol);
                 if (bnz) {
                     bulk_g2s(col_of(s), col + ak, bnz * 4u, &full[s], pol);
                     bulk_g2s(val_of(s), val + ak, bnz * (uint32_t)sizeof(VT), &full[s], pol);
                 }
+                for (int k = 0; k < NV; ++k) {
+                        const uint32_t vb = (uint32_t)epi.vbytes(k);
+                        bulk_g2s(vec_of(s, k), static_cast<const unsigned char*>(epi.vptr(k)) + (size_t)ar * vb,
+                                 (uint32_t)(vre - ar) * vb, &full[s]);
+                    }
+                cur = nxt;
+                if (i + 2 <= count) nxt = tiles[t0 + i + 2];
             };
-            for (int i = 0; i < first; ++i) issue(i);
+            // Without row-indexed vectors a tile depends only on the constant
+            // matrix: fetch the first tiles before waiting for the preceding
+            // kernel.  With vectors (written by earlier kernels) wait first.
+            int issued = 0;
+            if (NV == 0) {
+                for (; issued < first; ++issued) issue(issued);
+            }
             pdl_wait();
             stop = skip && *(volatile const int*)skip;
             if (!stop)
-                for (int i = first; i < count; ++i) {
-                    if (!mbar_wait(&empty[i % kStages], ((i / kStages) - 1) & 1)) break;
+                for (int i = issued; i < count; ++i) {
+                    if (i >= kStages && !mbar_wait(&empty[i % kStages], ((i / kStages) - 1) & 1)) break;
                     issue(i);
                 }
         }
     } else {
         pdl_wait();
         stop = skip && *(volatile const int*)skip;
-        const int n = stop ? first : count;
+        const int n = stop ? (NV == 0 ? first : 0) : count;  // tiles the producer issues
         const int grp = tid / vw, lane = tid - grp * vw;
+        const int ngroups = kCons / vw;
         for (int i = 0; i < n; ++i) {
             const int s = i % kStages;
             if (!mbar_wait(&full[s], (i / kStages) & 1)) break;
@@ -175,22 +212,29 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                 const int* rp = rp_of(s);
                 const int* cs = col_of(s);
                 const VT* vs = val_of(s);
-                const int row = inf.x + grp;
-                const bool active = row < inf.y;
-                typename Epi::Pre pre{};
-                if (active && lane == 0) pre = epi.load(row);
-                acc_t sum = acc_t(0);
-                if (active) {
-                    const int kb = rp[row - inf.z] - inf.w, ke = rp[row + 1 - inf.z] - inf.w;
+                VecTile vt;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) vt.base[k] = (k < NV) ? vec_of(s, k) : nullptr;
+                vt.row0 = inf.z;
+                const int nrows = inf.y - inf.x;
+                for (int rb = 0; rb < nrows; rb += ngroups) {  // same trip count in every lane
+                    const int row = inf.x + rb + grp;
+                    const bool active = rb + grp < nrows;
+                    typename Epi::Pre pre{};
+                    if (active && lane == 0) pre = epi.load(row, vt);
+                    acc_t sum = acc_t(0);
+                    if (active) {
+                        const int kb = rp[row - inf.z] - inf.w, ke = rp[row + 1 - inf.z] - inf.w;
 #pragma unroll 4
-                    for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
-                }
-                for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
-                if (active && lane == 0) {
-                    double e0 = 0.0, e1 = 0.0;
-                    epi.store(row, sum, pre, e0, e1);
-                    d0 += e0;
-                    d1 += e1;
+                        for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
+                    }
+                    for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
+                    if (active && lane == 0) {
+                        double e0 = 0.0, e1 = 0.0;
+                        epi.store(row, sum, pre, e0, e1);
+                        d0 += e0;
+                        d1 += e1;
+                    }
                 }
             }
             __syncwarp();
@@ -238,7 +282,12 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     const int k0 = rp[0], k1 = rp[nr];
     const bool warp_rows = (k1 - k0) >= 24 * nr;  // long rows: a warp per row
     typename Epi::Pre pre{};
-    if (tid < nr) pre = epi.load(r0 + tid);
+    VecTile vt;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        vt.base[k] = (k < Epi::nvec) ? static_cast<const unsigned char*>(epi.vptr(k)) : nullptr;
+    vt.row0 = 0;
+    if (tid < nr) pre = epi.load(r0 + tid, vt);
 
     acc_t acc = acc_t(0);
     for (int c0 = k0; c0 < k1; c0 += kTileNnz) {
@@ -318,32 +367,39 @@ int read_and_clear_dev_err() {
     return v;
 }
 
+template <typename VT, typename Epi, int RMAX>
+static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
+                          const int* skip, cudaStream_t s) {
+    const int grid = stream_grid(A.ntiles);
+    if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
+    const size_t smem = StreamLayout<VT, RMAX, Epi::nvec>::total;
+    static bool configured = false;  // once per template instance
+    if (!configured) {
+        AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kCons + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_stream<VT, Epi, RMAX>, (const int32_t*)A.ptr, (const int32_t*)A.col,
+                                val, (const int2*)A.tiles, (int)A.ntiles, (int)A.vw, epi, red, skip));
+}
+
 template <typename VT, typename Epi>
 static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
                 const int* skip, cudaStream_t s) {
     if (A.nrows == 0) return;
     if (A.tiles) {
-        const int grid = stream_grid(A.ntiles);
-        if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
-        static bool configured = false;  // per template instance
-        const size_t smem = StreamLayout<VT>::total;
-        if (!configured) {
-            AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            configured = true;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kCons + 32);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = g_pdl ? 1 : 0;
-        AMG_CUDA(cudaLaunchKernelEx(&cfg, k_stream<VT, Epi>, (const int32_t*)A.ptr, (const int32_t*)A.col,
-                                    val, (const int2*)A.tiles, (int)A.ntiles, (int)A.vw, epi, red, skip));
+        if (A.rows_cap <= 256) launch_stream<VT, Epi, 256>(A, val, epi, red, skip, s);
+        else launch_stream<VT, Epi, 512>(A, val, epi, red, skip, s);
         return;
     }
     if (Epi::ndot > 0 && A.nblk > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
@@ -373,12 +429,13 @@ void launch_spmv_dot2(const DevCsr& A, const double* x, const double* w, double*
 
 void launch_presmooth_residual(const DevCsr& A, const double* d, const double* f, double* x,
                                double* t, const int* skip, cudaStream_t s) {
-    run(A, A.val, EpiPre{d, f, x, t}, Reduce{}, skip, s);
+    run(A, A.vald, EpiPre{d, f, x, t}, Reduce{}, skip, s);
 }
 
 void launch_smooth(const DevCsr& A, const double* d, const double* f, const double* x, double* y,
                    const double* w, const Reduce* r, const int* skip, cudaStream_t s) {
-    if (r) run(A, A.val, EpiSmooth<true>{d, f, x, y, w}, *r, skip, s);
+    if (r && w == f) run(A, A.val, EpiSmoothDotF{d, f, x, y}, *r, skip, s);
+    else if (r) run(A, A.val, EpiSmooth<true>{d, f, x, y, w}, *r, skip, s);
     else run(A, A.val, EpiSmooth<false>{d, f, x, y, nullptr}, Reduce{}, skip, s);
 }
 
@@ -399,7 +456,7 @@ void launch_spmv_f32(const DevCsr& A, const float* x, float* y, const int* skip,
 void launch_presmooth_residual_f32(const DevCsr& A, const float* d, const float* f32,
                                    const double* f64, float* x, float* t, const int* skip,
                                    cudaStream_t s) {
-    run(A, A.val32, EpiPre32{d, f32, f64, x, t}, Reduce{}, skip, s);
+    run(A, A.vald32, EpiPre32{d, f32, f64, x, t}, Reduce{}, skip, s);
 }
 
 void launch_smooth_f32(const DevCsr& A, const float* d, const float* f32, const double* f64,
