@@ -58,6 +58,7 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
 constexpr int kThreads = 256;
 constexpr int kRowsPerBlock = 256;
 constexpr int kTileNnz = 2048;
+constexpr int kConsumers = 256;  // consumer threads per CTA of the streaming engine
 
 struct DevCsr {
     int32_t nrows = 0, ncols = 0;

@@ -37,7 +37,7 @@ namespace amg {
 // dependent launch the producer fetches its first tiles -- constant matrix
 // data -- before waiting for the previous kernel, so consecutive kernels of
 // the solve overlap their pipeline fill with the predecessor's tail.
-constexpr int kCons = 256;      // consumer threads per CTA
+constexpr int kCons = kConsumers;
 constexpr int kStages = 3;
 constexpr int kCtasPerSm = 2;
 
