@@ -171,6 +171,26 @@ amg_status amg_level_spmv(amg_handle *h, int level, int which, const double *x, 
  * (deterministic).  Errors: INVALID_ARG, OOM, CUDA. */
 amg_status amg_spmv_dot(const amg_csr *A, const double *x, double *y, double *dot, void *stream);
 
+/* amg_spmv_dot without allocating: the same product, dot and checks, for
+ * callers that cannot allocate device memory while they run (a
+ * latency-critical loop that cannot afford the allocator's locks and possible
+ * device synchronisation, a process whose device memory is reserved up front
+ * by another allocator, or rules that forbid dynamic allocation after
+ * initialisation).  The paper has no counterpart; this is an interface
+ * convenience.  Scratch lives in a static device array of the library, about
+ * 1 MiB, that every GPU loading the library keeps until the process exits;
+ * the call makes no cudaMalloc, cudaFree or other allocating call.  Limit:
+ * the matrix may span at most 65,536 row blocks (n up to 16,777,216 rows when
+ * rows average at most 8 nonzeros; fewer rows for longer rows); above that
+ * the call returns AMG_ERR_TOO_LARGE.  The first call on a device looks up
+ * the array's device address (make that first call before any stream
+ * capture).  All calls in the process share the one array, and it keeps the
+ * previous call's contents (the call clears what must start at zero): calls
+ * that overlap on the GPU race and must be ordered by the caller.  Results
+ * are identical to amg_spmv_dot's.  Errors: INVALID_ARG, TOO_LARGE, CUDA. */
+amg_status amg_spmv_dot_noalloc(const amg_csr *A, const double *x, double *y, double *dot,
+                                void *stream);
+
 /* Kernel classes reported by amg_solve_profile. */
 typedef enum {
     AMG_KC_SPMV_DOT = 0,      /* q = A p with p.q (a1) */

@@ -78,6 +78,7 @@ _sigs = {
     "amg_apply_precond": [_VP, _VP, _VP],
     "amg_level_spmv": [_VP, _I, _I, _VP, _VP],
     "amg_spmv_dot": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
+    "amg_spmv_dot_noalloc": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
 }
@@ -244,6 +245,14 @@ def amg_level_spmv(h, level, which, x, y):
 def amg_spmv_dot(csr: amg_csr, x, y, dot, stream=None):
     _check(_lib.amg_spmv_dot(C.byref(csr), _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
            "amg_spmv_dot")
+
+
+def amg_spmv_dot_noalloc(csr: amg_csr, x, y, dot, stream=None):
+    """amg_spmv_dot for callers that cannot allocate: scratch is a fixed static
+    device array of the library (see include/amg.h for the size limit and the
+    rule that overlapping calls race)."""
+    _check(_lib.amg_spmv_dot_noalloc(C.byref(csr), _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
+           "amg_spmv_dot_noalloc")
 
 
 # ------------------------------------------------------------- convenience

@@ -46,6 +46,7 @@ void dev_free(void* p) {
 }
 
 void build_hierarchy(amg_handle* h, HostCsr A);
+amg_status spmv_dot_noalloc(const amg_csr* A, const double* x, double* y, double* dot, void* stream);
 amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int maxiter,
                      int* iters, double* relres, Issue* prof);
 void run_vcycle(amg_handle* h, const double* r, double* z);
@@ -396,6 +397,11 @@ amg_status amg_spmv_dot(const amg_csr* A, const double* x, double* y, double* do
         AMG_CUDA(cudaStreamSynchronize(s));
         return result;
     });
+}
+
+amg_status amg_spmv_dot_noalloc(const amg_csr* A, const double* x, double* y, double* dot,
+                                void* stream) {
+    return guarded([&]() -> amg_status { return spmv_dot_noalloc(A, x, y, dot, stream); });
 }
 
 }  // extern "C"
