@@ -81,6 +81,10 @@ typedef struct {
     int use_pdl;           /* [1] let consecutive sparse-product kernels overlap through
                               programmatic dependent launch (process-wide setting, applied
                               at each call that launches work) */
+    int use_tail;          /* [0] run the small coarse levels (below about 4 million nonzeros,
+                              finest level excluded) as one cooperative launch with grid-wide
+                              barriers; applies when npre = npost = 1.  Off by default: inside
+                              the solve's CUDA graph the separate launches were faster. */
 } amg_params;
 
 /* A CSR matrix as passed in by the caller (see the conventions above). */

@@ -50,6 +50,7 @@ class amg_params(C.Structure):
         ("use_graph", C.c_int),
         ("use_stream", C.c_int),
         ("use_pdl", C.c_int),
+        ("use_tail", C.c_int),
     ]
 
 

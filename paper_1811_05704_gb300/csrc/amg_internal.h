@@ -200,6 +200,32 @@ void launch_coarse_solve_f32(const double* inv, int32_t n, const float* f, float
 void launch_copy_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 void launch_validate_csr(int32_t n, int64_t nnz, const int32_t* ptr, int* err, cudaStream_t s);
 
+// Small coarse levels in one cooperative launch (tail.cu).
+enum TailOp : int { TAIL_PRE = 0, TAIL_SPMV = 1, TAIL_COARSE = 2, TAIL_PROLONG = 3, TAIL_POST = 4 };
+struct TailPhase {
+    int op;             // TailOp
+    int n;              // rows
+    int vw;             // lanes per row
+    int ncols;          // columns of the dense inverse (TAIL_COARSE)
+    const int32_t* ptr;
+    const int32_t* col;
+    const void* val;    // matrix values (scaled by d_j for TAIL_PRE)
+    const double* inv;  // dense inverse (TAIL_COARSE)
+    const void* d;      // smoother diagonal
+    const void* f;      // right-hand side of the level
+    const void* xin;    // gathered input vector
+    void* out1;
+    void* out2;
+};
+struct TailPlan {
+    TailPhase* phases = nullptr;  // device array
+    int nph = 0;
+    unsigned int* bar = nullptr;  // grid barrier state, 2 words
+    int* err = nullptr;           // device error word
+};
+void launch_tail(const TailPlan& plan, bool f32, const int* skip, cudaStream_t s);
+int* dev_err_ptr();
+
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.
 void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s);

@@ -40,6 +40,7 @@ template double* dev_alloc<double>(size_t);
 template float* dev_alloc<float>(size_t);
 template unsigned int* dev_alloc<unsigned int>(size_t);
 template KState* dev_alloc<KState>(size_t);
+template TailPhase* dev_alloc<TailPhase>(size_t);
 
 void dev_free(void* p) {
     if (p) cudaFree(p);
@@ -132,6 +133,7 @@ amg_status amg_params_default(amg_params* p) {
     p->use_graph = 1;
     p->use_stream = 1;
     p->use_pdl = 1;
+    p->use_tail = 0;
     return AMG_OK;
 }
 

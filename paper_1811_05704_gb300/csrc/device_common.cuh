@@ -52,7 +52,7 @@ __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
 // Krylov scalar recurrences, executed by one thread once the dot products of
 // the current kernel are complete.  CG follows preconditioned CG (Saad,
 // Alg. 9.1); BiCGStab the right-preconditioned form (Saad, Alg. 7.7).
-__device__ void finalize(const Reduce& red, double a, double b) {
+static __device__ void finalize(const Reduce& red, double a, double b) {
     KState* st = red.st;
     switch (red.fin) {
         case FIN_NONE:
@@ -149,7 +149,7 @@ __device__ void finalize(const Reduce& red, double a, double b) {
 // Per-block partial sums -> partial[], and the last block to finish sums the
 // partials in index order and runs finalize().  Deterministic for a given
 // grid size.  Must be reached by every thread of every block of the grid.
-__device__ void reduce_finalize(const Reduce& red, double a, double b) {
+static __device__ void reduce_finalize(const Reduce& red, double a, double b) {
     __shared__ double sh[32];
     __shared__ int last;
     const double ta = block_sum(a, sh);

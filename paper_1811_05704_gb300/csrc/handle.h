@@ -58,6 +58,8 @@ struct amg_handle {
     std::vector<amg::Level> lev;
     double* cinv = nullptr;           // dense inverse of the coarsest matrix
     int32_t nc = 0;
+    int tail_ls = 0;                  // first level run by the tail kernel (0: none)
+    amg::TailPlan tail64, tail32;
     // Krylov vectors (length n)
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rh = nullptr, *v = nullptr,
            *ph = nullptr, *sv = nullptr, *sh = nullptr, *tv = nullptr, *fbuf = nullptr,

@@ -80,6 +80,80 @@ static void download(const DevCsr& D, HostCsr& H) {
     AMG_CUDA(cudaMemcpy(H.val.data(), D.val, D.nnz * sizeof(double), cudaMemcpyDeviceToHost));
 }
 
+// Lanes per row for the tail kernel's plain-load rows: about a quarter of the
+// mean row length, a power of two in [1, 32].
+static int tail_vw(const DevCsr& D) {
+    const double avg = D.nrows ? (double)D.nnz / (double)D.nrows : 1.0;
+    int vw = 1;
+    while (vw < 32 && 2.0 * vw <= avg / 4.0) vw *= 2;
+    return vw;
+}
+
+constexpr int64_t kTailMaxNnz = 4 << 20;
+
+// Phases of the tail kernel: levels ls..L-2 down (pre-sweep + residual,
+// restriction), the dense coarsest solve, levels L-2..ls up (prolongation +
+// correction, post-sweep).  Only with one pre- and one post-sweep.
+static void build_tail(amg_handle* h) {
+    const int nl = (int)h->lev.size();
+    h->tail_ls = 0;
+    if (!h->prm.use_tail || h->prm.npre != 1 || h->prm.npost != 1 || nl < 3) return;
+    int ls = 0;
+    for (int l = 1; l < nl - 1; ++l)
+        if (h->lev[l].A.nnz <= kTailMaxNnz) { ls = l; break; }
+    if (ls == 0) return;
+    const bool f32 = h->prm.precision == AMG_PRECISION_FP32;
+    for (int pass = 0; pass < (f32 ? 2 : 1); ++pass) {
+        const bool p32 = pass == 1;
+        std::vector<TailPhase> ph;
+        auto V = [&](double* a, float* b) -> void* { return p32 ? (void*)b : (void*)a; };
+        for (int l = ls; l < nl - 1; ++l) {
+            Level& v = h->lev[l];
+            Level& c = h->lev[l + 1];
+            TailPhase pre = {};
+            pre.op = TAIL_PRE; pre.n = v.A.nrows; pre.vw = tail_vw(v.A);
+            pre.ptr = v.A.ptr; pre.col = v.A.col; pre.val = p32 ? (const void*)v.A.vald32 : (const void*)v.A.vald;
+            pre.d = p32 ? (const void*)v.d32 : (const void*)v.d; pre.f = V(v.f, v.f32);
+            pre.out1 = V(v.x, v.x32); pre.out2 = V(v.t, v.t32);
+            ph.push_back(pre);
+            TailPhase rs = {};
+            rs.op = TAIL_SPMV; rs.n = v.R.nrows; rs.vw = tail_vw(v.R);
+            rs.ptr = v.R.ptr; rs.col = v.R.col; rs.val = p32 ? (const void*)v.R.val32 : (const void*)v.R.val;
+            rs.xin = V(v.t, v.t32); rs.out1 = V(c.f, c.f32);
+            ph.push_back(rs);
+        }
+        Level& cl = h->lev[nl - 1];
+        TailPhase co = {};
+        co.op = TAIL_COARSE; co.n = h->nc; co.ncols = h->nc; co.inv = h->cinv;
+        co.f = V(cl.f, cl.f32); co.out1 = V(cl.x, cl.x32);
+        ph.push_back(co);
+        for (int l = nl - 2; l >= ls; --l) {
+            Level& v = h->lev[l];
+            Level& c = h->lev[l + 1];
+            TailPhase pr = {};
+            pr.op = TAIL_PROLONG; pr.n = v.P.nrows; pr.vw = tail_vw(v.P);
+            pr.ptr = v.P.ptr; pr.col = v.P.col; pr.val = p32 ? (const void*)v.P.val32 : (const void*)v.P.val;
+            pr.xin = (l + 1 == nl - 1) ? V(c.x, c.x32) : V(c.y, c.y32);
+            pr.out1 = V(v.x, v.x32);
+            ph.push_back(pr);
+            TailPhase po = {};
+            po.op = TAIL_POST; po.n = v.A.nrows; po.vw = tail_vw(v.A);
+            po.ptr = v.A.ptr; po.col = v.A.col; po.val = p32 ? (const void*)v.A.val32 : (const void*)v.A.val;
+            po.d = p32 ? (const void*)v.d32 : (const void*)v.d; po.f = V(v.f, v.f32);
+            po.xin = V(v.x, v.x32); po.out1 = V(v.y, v.y32);
+            ph.push_back(po);
+        }
+        TailPlan& plan = p32 ? h->tail32 : h->tail64;
+        plan.nph = (int)ph.size();
+        plan.phases = halloc<TailPhase>(h, ph.size());
+        AMG_CUDA(cudaMemcpy(plan.phases, ph.data(), ph.size() * sizeof(TailPhase), cudaMemcpyHostToDevice));
+        plan.bar = halloc<unsigned int>(h, 2);
+        AMG_CUDA(cudaMemset(plan.bar, 0, 2 * sizeof(unsigned int)));
+        plan.err = dev_err_ptr();
+    }
+    h->tail_ls = ls;
+}
+
 // ------------------------------------------------------------- setup
 // Algorithm 1.  Stop rule: a level with at most coarse_enough rows, the
 // max_levels-th level, or a level whose aggregation keeps >= 95% of the rows
@@ -190,6 +264,7 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         }
     }
     AMG_CUDA(cudaStreamSynchronize(h->stream));
+    build_tail(h);
 }
 
 // ------------------------------------------------------------ issuing
@@ -225,7 +300,9 @@ static void issue_vcycle64(amg_handle* h, Issue& I, const double* r, double* z, 
     const int npre = h->prm.npre, npost = h->prm.npost;
     cudaStream_t s = I.s;
     std::vector<double*> cur(nl, nullptr);
-    for (int l = 0; l < nl - 1; ++l) {
+    const int ls = h->tail_ls;  // levels >= ls run in the tail kernel
+    const int down_end = ls ? ls : nl - 1;
+    for (int l = 0; l < down_end; ++l) {
         Level& v = L[l];
         const int64_t n = v.A.nrows;
         const double* f = (l == 0) ? r : v.f;
@@ -258,11 +335,16 @@ static void issue_vcycle64(amg_handle* h, Issue& I, const double* r, double* z, 
         if (rz) { I.pre(AMG_KC_OTHER); launch_dot2(*rz, r, z, nullptr, nullptr, h->n, skip, s); I.post(); }
         return;
     }
-    Level& c = L[nl - 1];
-    I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve(h->cinv, h->nc, c.f, c.x, skip, s); I.post();
     std::vector<double*> out(nl, nullptr);
-    out[nl - 1] = c.x;
-    for (int l = nl - 2; l >= 0; --l) {
+    if (ls) {
+        I.pre(AMG_KC_VCYCLE_COARSER); launch_tail(h->tail64, false, skip, s); I.post();
+        out[ls] = L[ls].y;
+    } else {
+        Level& c = L[nl - 1];
+        I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve(h->cinv, h->nc, c.f, c.x, skip, s); I.post();
+        out[nl - 1] = c.x;
+    }
+    for (int l = (ls ? ls : nl - 1) - 1; l >= 0; --l) {
         Level& v = L[l];
         const double* f = (l == 0) ? r : v.f;
         const int kc = l == 0 ? AMG_KC_PROLONG_L0 : AMG_KC_VCYCLE_COARSER;
@@ -298,7 +380,8 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
     const int nl = (int)L.size();
     cudaStream_t s = I.s;
     if (nl == 1) { issue_vcycle64(h, I, r, z, skip, rz); return; }
-    for (int l = 0; l < nl - 1; ++l) {
+    const int ls = h->tail_ls;
+    for (int l = 0; l < (ls ? ls : nl - 1); ++l) {
         Level& v = L[l];
         const int kcp = l == 0 ? AMG_KC_PRESMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
         const int kcr = l == 0 ? AMG_KC_RESTRICT_L0 : AMG_KC_VCYCLE_COARSER;
@@ -308,10 +391,16 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
         I.post();
         I.pre(kcr); launch_spmv_f32(v.R, v.t32, L[l + 1].f32, skip, s); I.post();
     }
-    Level& c = L[nl - 1];
-    I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve_f32(h->cinv, h->nc, c.f32, c.x32, skip, s); I.post();
-    const float* below = c.x32;
-    for (int l = nl - 2; l >= 0; --l) {
+    const float* below = nullptr;
+    if (ls) {
+        I.pre(AMG_KC_VCYCLE_COARSER); launch_tail(h->tail32, true, skip, s); I.post();
+        below = L[ls].y32;
+    } else {
+        Level& c = L[nl - 1];
+        I.pre(AMG_KC_COARSE_SOLVE); launch_coarse_solve_f32(h->cinv, h->nc, c.f32, c.x32, skip, s); I.post();
+        below = c.x32;
+    }
+    for (int l = (ls ? ls : nl - 1) - 1; l >= 0; --l) {
         Level& v = L[l];
         const int kc = l == 0 ? AMG_KC_PROLONG_L0 : AMG_KC_VCYCLE_COARSER;
         const int kcs = l == 0 ? AMG_KC_POSTSMOOTH_L0 : AMG_KC_VCYCLE_COARSER;

@@ -75,17 +75,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
+        : "r"(smem_u32(b)), "r"(parity), "r"(100000u)  // suspend up to 100 us per poll
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls (seconds), records bit 2 in
-// g_dev_err and returns false instead of spinning forever.
+// Bounded wait: each poll suspends for at most 100 us, and after 2^15 polls
+// (at most about 3.3 s) the wait gives up, records bit 2 in g_dev_err and
+// returns false instead of spinning forever.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i)
+    for (uint32_t i = 0; i < (1u << 15); ++i)
         if (mbar_try(b, parity)) return true;
     atomicOr(&g_dev_err, 4);
     return false;
@@ -354,6 +355,12 @@ int stream_grid(int ntiles) {
         AMG_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
     }
     return std::max(1, std::min(ntiles, kCtasPerSm * g_sm_count));
+}
+
+int* dev_err_ptr() {
+    void* p = nullptr;
+    AMG_CUDA(cudaGetSymbolAddress(&p, g_dev_err));
+    return static_cast<int*>(p);
 }
 
 void enqueue_dev_err_copy(int* host_dst, cudaStream_t s) {

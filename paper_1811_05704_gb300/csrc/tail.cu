@@ -1,0 +1,141 @@
+// tail.cu -- the small coarse levels of the V-cycle in one launch.
+//
+// Below a few million nonzeros a level's sparse products take a few
+// microseconds of memory traffic but each separate launch costs about as much
+// again in launch and pipeline-fill latency.  The tail kernel therefore runs
+// Algorithm 2 from level ls down to the coarsest level and back up to ls as a
+// list of phases -- pre-sweep + residual, restriction, dense coarsest solve,
+// prolongation + correction, post-sweep -- in one cooperative launch, with a
+// grid-wide barrier between phases.  The data of these levels is small enough
+// to stay in L2, so rows are read with plain loads by warps (vw lanes per
+// row) rather than streamed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "amg_internal.h"
+#include "device_common.cuh"
+
+namespace amg {
+
+// Grid-wide barrier for a cooperative launch: bar[0] counts arrivals, bar[1]
+// is the generation.  The wait is bounded (2 s after arrival); on timeout bit
+// 8 is recorded in *err and the block continues (results are then reported
+// invalid by the host).
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+            while (*gen == g) {
+                __nanosleep(64);
+                uint64_t t;
+                asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+                if (t - t0 > 2000000000ull) {
+                    atomicOr(err, 8);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename VT, typename T>
+__global__ void __launch_bounds__(256)
+k_tail(const TailPhase* __restrict__ phases, int nph, unsigned int* bar, int* err,
+       const int* __restrict__ skip) {
+    if (skip && *skip) return;  // the same flag value in every block: uniform
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int p = 0; p < nph; ++p) {
+        const TailPhase P = phases[p];
+        const T* f = static_cast<const T*>(P.f);
+        const T* xin = static_cast<const T*>(P.xin);
+        const T* d = static_cast<const T*>(P.d);
+        T* out1 = static_cast<T*>(P.out1);
+        T* out2 = static_cast<T*>(P.out2);
+        if (P.op == TAIL_COARSE) {  // x = A_L^{-1} f, a warp per row of the dense inverse
+            for (int r = gw; r < P.n; r += nw) {
+                const double* a = P.inv + (int64_t)r * P.ncols;
+                double s = 0.0;
+                for (int j = lane; j < P.ncols; j += 32) s += a[j] * (double)f[j];
+                s = warp_sum(s);
+                if (lane == 0) out1[r] = (T)s;
+            }
+        } else {
+            const VT* val = static_cast<const VT*>(P.val);
+            const int vw = P.vw, per = 32 / vw;
+            const int sub = lane / vw, l2 = lane - sub * vw;
+            // gathered operand: f for the pre-sweep (values already scaled by
+            // d_j), the input vector otherwise
+            const T* g = (P.op == TAIL_PRE) ? f : xin;
+            for (int rb = gw * per; rb < P.n; rb += nw * per) {  // same trip count in the warp
+                const int r = rb + sub;
+                const bool act = r < P.n;
+                T s = T(0);
+                if (act)
+                    for (int k = P.ptr[r] + l2; k < P.ptr[r + 1]; k += vw) s += (T)val[k] * g[P.col[k]];
+                for (int o = vw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, vw);
+                if (act && l2 == 0) {
+                    switch (P.op) {
+                        case TAIL_PRE: {
+                            const T fr = f[r];
+                            out1[r] = d[r] * fr;  // x = d f
+                            out2[r] = fr - s;     // t = f - A x
+                            break;
+                        }
+                        case TAIL_SPMV: out1[r] = s; break;
+                        case TAIL_PROLONG: out1[r] += s; break;
+                        case TAIL_POST: out1[r] = xin[r] + d[r] * (f[r] - s); break;
+                        default: break;
+                    }
+                }
+            }
+        }
+        if (p + 1 < nph) grid_barrier(bar, err);
+    }
+}
+
+template <typename VT, typename T>
+static void launch_tail_t(const TailPlan& plan, const int* skip, cudaStream_t s) {
+    static int per_sm = 0;  // once per template instance
+    static int sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        AMG_CUDA(cudaGetDevice(&dev));
+        AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail<VT, T>, 256, 0));
+        per_sm = std::max(1, std::min(per_sm, 4));
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(per_sm * sms);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_tail<VT, T>, (const TailPhase*)plan.phases, plan.nph, plan.bar,
+                                plan.err, skip));
+}
+
+void launch_tail(const TailPlan& plan, bool f32, const int* skip, cudaStream_t s) {
+    if (f32) launch_tail_t<float, float>(plan, skip, s);
+    else launch_tail_t<double, double>(plan, skip, s);
+}
+
+}  // namespace amg

@@ -67,6 +67,7 @@ CASES = {
     "convdiff18": (lambda: gen.convdiff3d(18, seed=2)[0], {"solver": 1, "coarse_enough": 100}),
     "poisson2d_101": (lambda: gen.poisson2d_shift(101, 0.05), {"coarse_enough": 100}),
     "spai0_varcoef": (lambda: gen.varcoef3d(16, seed=3), {"smoother": 1, "coarse_enough": 50}),
+    "tail_varcoef20": (lambda: gen.varcoef3d(20, seed=1), {"coarse_enough": 40, "use_tail": 1}),
 }
 
 
@@ -304,7 +305,8 @@ def test_edge_cases(amg, torch_dev):
 
 def test_fp32_vcycle_reaches_fp64_tolerance(amg, torch_dev):
     import oracle
-    for A, kw in ((gen.poisson3d(32), {}), (gen.varcoef3d(24, seed=6), {"coarse_enough": 100})):
+    for A, kw in ((gen.poisson3d(32), {}), (gen.varcoef3d(24, seed=6), {"coarse_enough": 100}),
+                  (gen.varcoef3d(24, seed=6), {"coarse_enough": 40, "use_tail": 1})):
         f, _ = gen.rhs_from_solution(A, 8)
         S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=1, **kw)
         x = t(torch_dev, np.zeros(A.n))
