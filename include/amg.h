@@ -121,7 +121,8 @@ amg_status amg_setup(const amg_csr *A, const amg_params *prm, void *stream, amg_
  * *iters (may be NULL): iterations done.  *relres (may be NULL): true relative
  * residual ||f - A x||_2 / ||f||_2 in float64.  If ||f|| = 0: x = 0,
  * iters = 0, relres = 0.  Returns NOT_CONVERGED or BREAKDOWN with valid x,
- * iters and relres.  Synchronizes the handle's stream. */
+ * iters and relres; INVALID_ARG if f or the initial guess holds non-finite
+ * values (nothing is iterated).  Synchronizes the handle's stream. */
 amg_status amg_solve(amg_handle *h, const double *f, double *x, double rtol, int maxiter,
                      int *iters, double *relres);
 

@@ -651,6 +651,14 @@ amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int
             fail(AMG_ERR_CUDA, "a device pipeline wait timed out; results are invalid");
         }
         const KState& o = *h->st_out;
+        if (!std::isfinite(o.nf) || !std::isfinite(o.relres)) {
+            // nothing to iterate on: non-finite data in f or in the initial guess
+            if (iters) *iters = o.it;
+            if (relres) *relres = o.relres;
+            h->last_launches = launches;
+            if (o.it == 0) fail(AMG_ERR_INVALID_ARG, "f or the initial guess contains non-finite values");
+            return AMG_ERR_BREAKDOWN;
+        }
         if (o.zero_rhs) {
             AMG_CUDA(cudaMemsetAsync(x, 0, h->n * sizeof(double), h->stream));
             AMG_CUDA(cudaStreamSynchronize(h->stream));

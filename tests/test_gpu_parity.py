@@ -281,6 +281,22 @@ def test_edge_cases(amg, torch_dev):
     st, it, rr = S.solve(t(torch_dev, f), x)
     assert st == 0 and it == 0
     S.close()
+    # non-finite right-hand side or initial guess: refused, not iterated on
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, coarse_enough=50)
+    fn = f.copy()
+    fn[7] = np.nan
+    with pytest.raises(amg.AmgError) as e:
+        S.solve(t(torch_dev, fn), t(torch_dev, np.zeros(A.n)))
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    x0 = np.zeros(A.n)
+    x0[3] = np.inf
+    with pytest.raises(amg.AmgError) as e:
+        S.solve(t(torch_dev, f), t(torch_dev, x0))
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    # the handle stays usable
+    x = t(torch_dev, np.zeros(A.n))
+    assert S.solve(t(torch_dev, f), x)[0] == 0
+    S.close()
     # invalid inputs
     bad = gen.poisson3d(4)
     col = bad.col.copy()
