@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -218,6 +219,66 @@ def cpu_baseline_sample():
                       f"{dt:.2f} s, setup excluded)"}
 
 
+# ------------------------------------------------------------------ batched
+BATCH_SYSTEMS = 4096
+
+
+def bench_batched(amg, torch, dev, stream, args):
+    """4096 independent 2D Poisson systems (sides U{16..128}, shift U(0,0.1),
+    f ~ U(-1,1)), FP32 V-cycle under FP64 CG, rtol 1e-8, one persistent launch
+    with the autotuned schedule; against the plain FP64 single-system solve
+    (amg_solve per system) timed on an evenly spaced sample of the same
+    systems and scaled to all of them."""
+    sides, sigma = gen.batched_sides(BATCH_SYSTEMS, 0)
+    mats = [gen.poisson2d_shift(int(m), float(sg)) for m, sg in zip(sides, sigma)]
+    rhs = [gen.uniform_pm1(0, 1000 + k, A.n) for k, A in enumerate(mats)]
+    t0 = time.perf_counter()
+    b = amg.amg_batch_setup([amg.make_csr(A.n, A.row_ptr, A.col, A.val) for A in mats],
+                            amg.amg_params_default(precision=amg.AMG_PRECISION_FP32))
+    setup_s = time.perf_counter() - t0
+    tot, off, lev = amg.amg_batch_info(b, BATCH_SYSTEMS)
+    f = torch.from_numpy(np.concatenate(rhs)).to(dev)
+    x = torch.zeros(tot, dtype=torch.float64, device=dev)
+    threads, ctas = amg.amg_batch_tune(b, f, x, RTOL, MAXITER)
+    reps = max(3, args.steps // 4)
+    times = []
+    for _ in range(reps):
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, it, rr, sst = amg.amg_batch_solve(b, BATCH_SYSTEMS, f, x, RTOL, MAXITER)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        assert st == 0 and (rr <= RTOL).all()
+    amg.amg_batch_free(b)
+    batch_s = statistics.median(times)
+    # plain FP64 path: one handle and one solve per system, on a sample
+    sample = list(range(0, BATCH_SYSTEMS, BATCH_SYSTEMS // 128))
+    plain = 0.0
+    for k in sample:
+        A = mats[k]
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+        fk = torch.from_numpy(rhs[k]).to(dev)
+        xk = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        S.solve(fk, xk, RTOL, MAXITER)  # builds and caches the graph
+        xk.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        S.solve(fk, xk, RTOL, MAXITER)
+        plain += time.perf_counter() - t1
+        S.close()
+    plain_s = plain * BATCH_SYSTEMS / len(sample)
+    return {"workload": f"{BATCH_SYSTEMS} x 2D Poisson + shift, sides U{{16..128}}, FP32 V-cycle + FP64 CG",
+            "unknowns": int(tot), "setup_s": setup_s, "solve_s": batch_s,
+            "value": BATCH_SYSTEMS / batch_s, "unit": "systems/s",
+            "iterations_mean": float(np.mean(it)), "iterations_max": int(np.max(it)),
+            "levels_max": int(lev.max()), "schedule": {"threads": threads, "ctas_per_sm": ctas},
+            "plain_fp64_solve_s": plain_s,
+            "plain_note": f"amg_solve per system (FP64, CUDA graph) on {len(sample)} evenly spaced systems, scaled to {BATCH_SYSTEMS}",
+            "speedup_vs_plain": plain_s / batch_s}
+
+
 # ---------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -347,6 +408,10 @@ def main():
                  "relres": rr32, "status": st32, "precision": "fp32 V-cycle, fp64 CG"}
         S32.close()
 
+    batched = None
+    if not args.no_batch:
+        batched = bench_batched(amg, torch, dev, stream, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -373,6 +438,7 @@ def main():
         "solve_frac_of_peak": solve_gbs / peak,
         "kernels": per_kernel,
         "mixed": mixed,
+        "batched": batched,
         "clocks": clock_info,
         "cpu_baseline": cpu,
     }

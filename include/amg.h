@@ -176,6 +176,47 @@ amg_status amg_level_spmv(amg_handle *h, int level, int which, const double *x, 
  * (deterministic).  Errors: INVALID_ARG, OOM, CUDA. */
 amg_status amg_spmv_dot(const amg_csr *A, const double *x, double *y, double *dot, void *stream);
 
+/* ------------------------------------------------------------------
+ * Batched form: many independent systems, each with its own hierarchy,
+ * solved by one persistent launch.  A CTA takes the next system from a
+ * device work queue and runs its whole preconditioned CG (the same
+ * recurrences, stopping test and restart rule as amg_solve; Algorithm 2 as
+ * the preconditioner) with block-level synchronisation.  The V-cycle runs in
+ * the precision of the parameters (AMG_PRECISION_FP32: float32 V-cycle under
+ * float64 CG).  Supports CG with npre = npost = 1. */
+typedef struct amg_batch amg_batch;
+
+/* Set up nsys systems (Algorithm 1 for each; the per-system host work runs on
+ * a thread pool, and each level's Galerkin products of all systems run as one
+ * GPU product over their block-diagonal concatenation, which gives every
+ * system exactly its own hierarchy).  systems: nsys CSR matrices (host or
+ * device, each deep-copied).  Errors as amg_setup, for any system. */
+amg_status amg_batch_setup(int nsys, const amg_csr *systems, const amg_params *prm, void *stream,
+                           amg_batch **out);
+
+/* Solve all systems.  f, x: device, the systems' vectors concatenated in
+ * order (offsets from amg_batch_info); x holds the initial guesses and
+ * receives the solutions.  iters, relres, status: host arrays of nsys entries
+ * (each may be NULL): per-system iterations, true relative residual and
+ * status.  Returns the worst status over the systems (OK if all converged).
+ * Synchronizes the batch's stream. */
+amg_status amg_batch_solve(amg_batch *b, const double *f, double *x, double rtol, int maxiter,
+                           int *iters, double *relres, int *status);
+
+/* Autotune the schedule of amg_batch_solve: times candidate launch shapes
+ * (threads per CTA x CTAs per SM) and queue orders (largest system first, or
+ * input order) on these f and x, keeps the fastest for later solves and
+ * reports it (threads, ctas_per_sm may be NULL).  x is left solved. */
+amg_status amg_batch_tune(amg_batch *b, const double *f, double *x, double rtol, int maxiter,
+                          int *threads, int *ctas_per_sm);
+
+/* total_rows: sum of the systems' sizes; row_off: nsys + 1 offsets of the
+ * systems in f and x; levels: nsys level counts.  Outputs may be NULL. */
+amg_status amg_batch_info(const amg_batch *b, int64_t *total_rows, int64_t *row_off, int *levels);
+
+/* Release the batch and its device memory.  NULL is accepted. */
+amg_status amg_batch_free(amg_batch *b);
+
 /* amg_spmv_dot without allocating: the same product, dot and checks, for
  * callers that cannot allocate device memory while they run (a
  * latency-critical loop that cannot afford the allocator's locks and possible

@@ -82,6 +82,11 @@ _sigs = {
     "amg_spmv_dot_noalloc": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
+    "amg_batch_setup": [_I, _VP, C.POINTER(amg_params), _VP, C.POINTER(_VP)],
+    "amg_batch_solve": [_VP, _VP, _VP, _D, _I, _VP, _VP, _VP],
+    "amg_batch_tune": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_I)],
+    "amg_batch_info": [_VP, C.POINTER(_I64), _VP, _VP],
+    "amg_batch_free": [_VP],
 }
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
@@ -254,6 +259,46 @@ def amg_spmv_dot_noalloc(csr: amg_csr, x, y, dot, stream=None):
     rule that overlapping calls race)."""
     _check(_lib.amg_spmv_dot_noalloc(C.byref(csr), _ptr(x), _ptr(y), _ptr(dot), _stream(stream)),
            "amg_spmv_dot_noalloc")
+
+
+# ---------------------------------------------------------------- batched
+def amg_batch_setup(systems, params: amg_params = None, stream=None):
+    """systems: list of amg_csr (see make_csr).  Returns a batch handle."""
+    arr = (amg_csr * len(systems))(*systems)
+    h = C.c_void_p()
+    p = C.byref(params) if params is not None else None
+    _check(_lib.amg_batch_setup(len(systems), C.cast(arr, C.c_void_p), p, _stream(stream), C.byref(h)),
+           "amg_batch_setup")
+    return h
+
+
+def amg_batch_info(b, nsys):
+    tot = C.c_int64()
+    off = np.zeros(nsys + 1, np.int64)
+    lev = np.zeros(nsys, np.int32)
+    _check(_lib.amg_batch_info(b, C.byref(tot), off.ctypes.data, lev.ctypes.data), "amg_batch_info")
+    return tot.value, off, lev
+
+
+def amg_batch_solve(b, nsys, f, x, rtol=1e-8, maxiter=500):
+    """Returns (status, iters[nsys], relres[nsys], status[nsys])."""
+    it = np.zeros(nsys, np.int32)
+    rr = np.zeros(nsys, np.float64)
+    st = np.zeros(nsys, np.int32)
+    s = _lib.amg_batch_solve(b, _ptr(f), _ptr(x), rtol, maxiter, it.ctypes.data, rr.ctypes.data,
+                             st.ctypes.data)
+    _check(s, "amg_batch_solve", (AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_INVALID_ARG))
+    return s, it, rr, st
+
+
+def amg_batch_tune(b, f, x, rtol=1e-8, maxiter=500):
+    t, c = C.c_int(), C.c_int()
+    _check(_lib.amg_batch_tune(b, _ptr(f), _ptr(x), rtol, maxiter, C.byref(t), C.byref(c)), "amg_batch_tune")
+    return t.value, c.value
+
+
+def amg_batch_free(b):
+    _check(_lib.amg_batch_free(b), "amg_batch_free")
 
 
 # ------------------------------------------------------------- convenience

@@ -19,8 +19,8 @@ LIB_NAME = "libamg_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["spmv.cu", "spgemm.cu", "solver.cu", "capi.cu", "noalloc.cu", "tail.cu"]
-CPP_SOURCES = ["setup_host.cpp"]
+CU_SOURCES = ["spmv.cu", "spgemm.cu", "solver.cu", "capi.cu", "noalloc.cu", "tail.cu", "batch.cu"]
+CPP_SOURCES = ["setup_host.cpp", "batch_host.cpp"]
 
 
 def _cuda_home():

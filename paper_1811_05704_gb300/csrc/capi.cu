@@ -9,6 +9,7 @@
 #include <string>
 
 #include "amg_internal.h"
+#include "batch.h"
 #include "handle.h"
 
 namespace amg {
@@ -41,6 +42,10 @@ template float* dev_alloc<float>(size_t);
 template unsigned int* dev_alloc<unsigned int>(size_t);
 template KState* dev_alloc<KState>(size_t);
 template TailPhase* dev_alloc<TailPhase>(size_t);
+template unsigned char* dev_alloc<unsigned char>(size_t);
+template int64_t* dev_alloc<int64_t>(size_t);
+template BSys* dev_alloc<BSys>(size_t);
+template BResult* dev_alloc<BResult>(size_t);
 
 void dev_free(void* p) {
     if (p) cudaFree(p);
@@ -48,6 +53,34 @@ void dev_free(void* p) {
 
 void build_hierarchy(amg_handle* h, HostCsr A);
 amg_status spmv_dot_noalloc(const amg_csr* A, const double* x, double* y, double* dot, void* stream);
+void build_batch(amg_batch* b, const amg_csr* systems);
+
+static void free_batch(amg_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->res_host) cudaFreeHost(b->res_host);
+    delete b;
+}
+
+// Run the batch with the current schedule; fills res_host.  Returns the
+// worst status over the systems.
+static amg_status run_batch(amg_batch* b, const double* f, double* x, double rtol, int maxiter) {
+    launch_batch_cg(b->sys, b->order_mode == 0 ? b->order_by_size : b->order_input, b->nsys, b->row_off_dev,
+                    b->queue, f, x, rtol, maxiter, b->prm.precision == AMG_PRECISION_FP32, b->res,
+                    b->threads, b->ctas_per_sm, b->stream);
+    AMG_CUDA(cudaMemcpyAsync(b->res_host, b->res, b->nsys * sizeof(BResult), cudaMemcpyDeviceToHost, b->stream));
+    AMG_CUDA(cudaStreamSynchronize(b->stream));
+    int worst = AMG_OK;
+    for (int k = 0; k < b->nsys; ++k) {
+        const int st = b->res_host[k].status;
+        if (st == AMG_ERR_INVALID_ARG) worst = AMG_ERR_INVALID_ARG;
+        else if (st == AMG_ERR_BREAKDOWN && worst != AMG_ERR_INVALID_ARG) worst = AMG_ERR_BREAKDOWN;
+        else if (st == AMG_ERR_NOT_CONVERGED && worst == AMG_OK) worst = AMG_ERR_NOT_CONVERGED;
+    }
+    return (amg_status)worst;
+}
 amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int maxiter,
                      int* iters, double* relres, Issue* prof);
 void run_vcycle(amg_handle* h, const double* r, double* z);
@@ -398,6 +431,116 @@ amg_status amg_spmv_dot(const amg_csr* A, const double* x, double* y, double* do
         AMG_CUDA(cudaFreeAsync(scratch, s));
         AMG_CUDA(cudaStreamSynchronize(s));
         return result;
+    });
+}
+
+amg_status amg_batch_setup(int nsys, const amg_csr* systems, const amg_params* prm, void* stream,
+                           amg_batch** out) {
+    return guarded([&]() -> amg_status {
+        if (!out) fail(AMG_ERR_INVALID_ARG, "out is null");
+        *out = nullptr;
+        if (nsys < 1 || !systems) fail(AMG_ERR_INVALID_ARG, "nsys must be >= 1 and systems non-null");
+        amg_params p;
+        if (prm) p = *prm;
+        else amg_params_default(&p);
+        check_params(p);
+        if (p.npre != 1 || p.npost != 1 || p.solver != AMG_SOLVER_CG)
+            fail(AMG_ERR_INVALID_ARG, "the batched solve supports CG with one pre- and one post-sweep");
+        amg_batch* b = new amg_batch();
+        try {
+            b->prm = p;
+            b->nsys = nsys;
+            b->stream = static_cast<cudaStream_t>(stream);
+            AMG_CUDA(cudaGetDevice(&b->device));
+            build_batch(b, systems);
+        } catch (...) {
+            free_batch(b);
+            throw;
+        }
+        *out = b;
+        return AMG_OK;
+    });
+}
+
+amg_status amg_batch_solve(amg_batch* b, const double* f, double* x, double rtol, int maxiter, int* iters,
+                           double* relres, int* status) {
+    return guarded([&]() -> amg_status {
+        if (!b || !f || !x || f == x) fail(AMG_ERR_INVALID_ARG, "bad arguments");
+        if (!(rtol >= 0.0) || maxiter < 0) fail(AMG_ERR_INVALID_ARG, "rtol must be >= 0 and maxiter >= 0");
+        AMG_CUDA(cudaSetDevice(b->device));
+        const amg_status st = run_batch(b, f, x, rtol, maxiter);
+        for (int k = 0; k < b->nsys; ++k) {
+            if (iters) iters[k] = b->res_host[k].iters;
+            if (relres) relres[k] = b->res_host[k].relres;
+            if (status) status[k] = b->res_host[k].status;
+        }
+        return st;
+    });
+}
+
+amg_status amg_batch_tune(amg_batch* b, const double* f, double* x, double rtol, int maxiter, int* threads,
+                          int* ctas_per_sm) {
+    return guarded([&]() -> amg_status {
+        if (!b || !f || !x || f == x) fail(AMG_ERR_INVALID_ARG, "bad arguments");
+        AMG_CUDA(cudaSetDevice(b->device));
+        const int cand[][2] = {{128, 4}, {256, 2}, {256, 4}, {512, 1}, {512, 2}, {1024, 1}};
+        cudaEvent_t e0, e1;
+        AMG_CUDA(cudaEventCreate(&e0));
+        AMG_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bt = b->threads, bc = b->ctas_per_sm, bo = b->order_mode;
+        try {
+            const int maxt = batch_max_threads(b->prm.precision == AMG_PRECISION_FP32);
+            for (int order = 0; order < 2; ++order)
+                for (const auto& c : cand) {
+                    if (c[0] > maxt) continue;
+                    b->threads = c[0];
+                    b->ctas_per_sm = c[1];
+                    b->order_mode = order;
+                    AMG_CUDA(cudaMemsetAsync(x, 0, b->total_rows * sizeof(double), b->stream));
+                    AMG_CUDA(cudaEventRecord(e0, b->stream));
+                    run_batch(b, f, x, rtol, maxiter);
+                    AMG_CUDA(cudaEventRecord(e1, b->stream));
+                    AMG_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) { best = ms; bt = c[0]; bc = c[1]; bo = order; }
+                }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->threads = bt;
+        b->ctas_per_sm = bc;
+        b->order_mode = bo;
+        b->tuned = 1;
+        if (threads) *threads = bt;
+        if (ctas_per_sm) *ctas_per_sm = bc;
+        AMG_CUDA(cudaMemsetAsync(x, 0, b->total_rows * sizeof(double), b->stream));
+        run_batch(b, f, x, rtol, maxiter);  // leave x solved with the chosen schedule
+        return AMG_OK;
+    });
+}
+
+amg_status amg_batch_info(const amg_batch* b, int64_t* total_rows, int64_t* row_off, int* levels) {
+    return guarded([&]() -> amg_status {
+        if (!b) fail(AMG_ERR_INVALID_ARG, "null batch");
+        if (total_rows) *total_rows = b->total_rows;
+        for (int k = 0; k <= b->nsys; ++k) {
+            if (row_off) row_off[k] = b->row_off[k];
+            if (levels && k < b->nsys) levels[k] = b->levels[k];
+        }
+        return AMG_OK;
+    });
+}
+
+amg_status amg_batch_free(amg_batch* b) {
+    return guarded([&]() -> amg_status {
+        free_batch(b);
+        return AMG_OK;
     });
 }
 
