@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -279,6 +282,105 @@ def bench_batched(amg, torch, dev, stream, args):
             "speedup_vs_plain": plain_s / batch_s}
 
 
+def _serve_matrices(reqs):
+    """Matrices of a request stream, generated in parallel; varcoef and
+    convdiff matrices take the grid side as their seed, so one matrix per
+    (kind, side) is generated and shared by the keys that ask for it (each key
+    still gets its own hierarchy)."""
+    import concurrent.futures as cf
+    combos = sorted({(q.kind, q.side) for q in reqs})
+
+    def make(c):
+        kind, side = c
+        if kind == "poisson":
+            return gen.poisson3d(side)
+        if kind == "varcoef":
+            return gen.varcoef3d(side, seed=side, log10_range=gen.problems.SERVE_VARCOEF_RANGE)
+        return gen.convdiff3d(side, seed=side)[0]
+
+    with cf.ThreadPoolExecutor(8) as ex:
+        return dict(zip(combos, ex.map(make, combos)))
+
+
+def bench_serving(amg, args):
+    """A stream of solve requests through the server: grid sides log-uniform
+    on [20, 160] (8,000 to 4,096,000 unknowns), 70% SPD (3D Poisson and
+    variable-coefficient diffusion with k = 10^U(-2,2), CG), 30% upwind convection-diffusion
+    (BiCGStab), 20% of the requests a new right-hand side for an earlier
+    request's matrix; every request is set up (unless its hierarchy is
+    resident) and solved to rtol 1e-8 from host memory.  Saturated
+    throughput (all requests queued at once) against the plain API serving
+    the same requests one after another (amg_setup + amg_solve_host, a
+    hierarchy kept until its key's last request), then latency under Poisson
+    arrivals at 70% of the saturated rate."""
+    nreq, slots = args.serve_requests, args.serve_slots
+    reqs = gen.serving_requests(nreq, SEED, lo=20, hi=160)
+    t0 = time.perf_counter()
+    mats = _serve_matrices(reqs)
+    gen_s = time.perf_counter() - t0
+    A_of = lambda q: mats[(q.kind, q.side)]  # noqa: E731
+    rhs = [q.rhs(SEED, A_of(q).n) for q in reqs]
+    csrs = {c: amg.make_csr(A.n, A.row_ptr, A.col, A.val) for c, A in mats.items()}
+    last_use = {q.key: q.index for q in reqs}
+    rows = sum(A_of(q).n for q in reqs)
+
+    # plain API, one request after another
+    handles, serial_status = {}, []
+    t0 = time.perf_counter()
+    for q in reqs:
+        if q.key not in handles:
+            handles[q.key] = amg.amg_setup(csrs[(q.kind, q.side)], amg.amg_params_default(solver=q.solver))
+        x = np.zeros(A_of(q).n)
+        serial_status.append(amg.amg_solve_host(handles[q.key], rhs[q.index], x, RTOL, MAXITER)[0])
+        if last_use[q.key] == q.index:
+            amg.amg_free(handles.pop(q.key))
+    serial_s = time.perf_counter() - t0
+
+    def run(arrival):
+        """Submit every request at its arrival time (None: all at once),
+        then collect the results."""
+        srv = amg.amg_server_create(slots=slots)
+        ids = []
+        t_start = time.perf_counter()
+        for q in reqs:
+            if arrival is not None:
+                delay = t_start + arrival[q.index] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            ids.append(amg.amg_server_submit(srv, q.key, csrs[(q.kind, q.side)], rhs[q.index], q.solver,
+                                             RTOL, MAXITER))
+        res = [amg.amg_server_wait(srv, rid, A_of(q).n) for q, rid in zip(reqs, ids)]
+        wall = time.perf_counter() - t_start
+        stats = amg.amg_server_stats(srv)
+        amg.amg_server_destroy(srv)
+        return wall, res, stats
+
+    sat_s, sat_res, sat_stats = run(None)
+    sat_rate = nreq / sat_s
+    # Poisson arrivals at 70% of the saturated rate (the stream's seeded draws at rate 1, rescaled)
+    rate = 0.7 * sat_rate
+    unit_arrivals = np.array([q.arrival for q in gen.serving_requests(nreq, SEED, lo=20, hi=160, rate=1.0)])
+    open_s, open_res, open_stats = run(unit_arrivals / rate)
+    lat = np.array([r[4] for r in open_res]) * 1e3
+    ok = all(r[0] == 0 and r[3] <= RTOL for r in sat_res + open_res) and all(s == 0 for s in serial_status)
+    failed = [{"index": q.index, "kind": q.kind, "side": q.side, "status": [r[0], o[0], serial_status[q.index]],
+               "iters": r[2], "relres": r[3]}
+              for q, r, o in zip(reqs, sat_res, open_res)
+              if r[0] != 0 or o[0] != 0 or serial_status[q.index] != 0 or r[3] > RTOL][:10]
+    same = all(np.array_equal(a[1], b[1]) for a, b in zip(sat_res, open_res))
+    return {"workload": f"{nreq} requests, sides log-uniform [20,160], 70% SPD (CG) / 30% convdiff (BiCGStab), "
+                        "20% reuse of an earlier matrix, rtol 1e-8, FP64, host vectors",
+            "requests": nreq, "rows_total": int(rows), "slots": slots, "all_converged": ok, "failed": failed,
+            "same_result_saturated_and_open_loop": same,
+            "value": sat_rate, "unit": "requests/s (setup + solve)", "saturated_s": sat_s,
+            "serial_plain_s": serial_s, "serial_plain_rate": nreq / serial_s, "speedup_vs_serial": serial_s / sat_s,
+            "open_loop_rate": rate, "open_loop_s": open_s,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "peak_charged_bytes": sat_stats["peak_bytes"], "evictions": sat_stats["evictions"],
+            "matrix_generation_s": gen_s}
+
+
 # ---------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -412,6 +514,10 @@ def main():
     if not args.no_batch:
         batched = bench_batched(amg, torch, dev, stream, args)
 
+    serving = None
+    if not args.no_serve:
+        serving = bench_serving(amg, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -439,6 +545,7 @@ def main():
         "kernels": per_kernel,
         "mixed": mixed,
         "batched": batched,
+        "serving": serving,
         "clocks": clock_info,
         "cpu_baseline": cpu,
     }

@@ -12,6 +12,7 @@ from .rng import uniform01, splitmix64_stream
 from .problems import (
     Csr,
     poisson3d,
+    poisson3d_star,
     poisson2d_shift,
     varcoef3d,
     convdiff3d,
@@ -20,6 +21,8 @@ from .problems import (
     poisson3d_nnz,
     batched_sides,
     serving_sides,
+    serving_requests,
+    ServeRequest,
 )
 
 __all__ = [
@@ -27,6 +30,7 @@ __all__ = [
     "splitmix64_stream",
     "Csr",
     "poisson3d",
+    "poisson3d_star",
     "poisson2d_shift",
     "varcoef3d",
     "convdiff3d",
@@ -35,4 +39,6 @@ __all__ = [
     "poisson3d_nnz",
     "batched_sides",
     "serving_sides",
+    "serving_requests",
+    "ServeRequest",
 ]

@@ -25,6 +25,12 @@ STREAM_VEL = 3
 STREAM_SHIFT = 4
 STREAM_USTAR = 10
 STREAM_RHS = 11
+STREAM_KIND = 20
+STREAM_REUSE = 21
+STREAM_PICK = 22
+STREAM_ARRIVAL = 23
+STREAM_REQ_RHS = 100000  # + request index
+SERVE_VARCOEF_RANGE = (-2.0, 2.0)  # log10 of the cell coefficients of served SPD requests
 
 
 @dataclass
@@ -82,6 +88,34 @@ def poisson3d(m: int) -> Csr:
     cols = [idx + o for o in offs]
     vals = [np.full(n, -1.0) if o != 0 else np.full(n, 6.0) for o in offs]
     return _assemble(n, offs, cols, vals, masks)
+
+
+def poisson3d_star(m: int, w: float = 1.0) -> Csr:
+    """poisson3d(m) plus a star: node 0 coupled to every other node with weight
+    w (graph-Laplacian entries: -w off the diagonal, +w on node j's diagonal,
+    (n-1) w on node 0's).  SPD, with one dense row and column, so the coarse
+    operators carry a row as wide as the coarse level (an edge case of the
+    Galerkin product)."""
+    P = poisson3d(m)
+    n = P.n
+    rows = np.repeat(np.arange(n), np.diff(P.row_ptr))
+    cols = P.col.astype(np.int64)
+    vals = P.val.copy()
+    vals[(rows == cols) & (rows > 0)] += w
+    vals[(rows == 0) & (cols == 0)] += (n - 1) * w
+    # the star's off-diagonal entries not already present in the stencil
+    have0 = set(cols[rows == 0].tolist())
+    extra = np.array([j for j in range(1, n) if j not in have0], dtype=np.int64)
+    vals[(rows == 0) & (cols > 0)] += -w
+    vals[(cols == 0) & (rows > 0)] += -w
+    r = np.concatenate([rows, np.zeros(len(extra), np.int64), extra])
+    c = np.concatenate([cols, extra, np.zeros(len(extra), np.int64)])
+    v = np.concatenate([vals, np.full(len(extra), -w), np.full(len(extra), -w)])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=row_ptr[1:])
+    return Csr(n, row_ptr.astype(np.int32), c.astype(np.int32), v)
 
 
 def poisson2d_shift(m: int, sigma: float) -> Csr:
@@ -199,3 +233,60 @@ def serving_sides(count: int, seed: int, lo: int = 20, hi: int = 160):
     """Per-request grid sides, log-uniform on [lo, hi] (so unknowns log-uniform too)."""
     u = uniform01(seed, STREAM_COEF, count)
     return np.rint(np.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * u)).astype(np.int64)
+
+
+@dataclass
+class ServeRequest:
+    """One request of a served stream: the key of its matrix, the matrix's
+    kind ('poisson' or 'varcoef' with coefficients 10^U(-2,2): SPD, solved by CG; 'convdiff':
+    nonsymmetric, solved by BiCGStab), its grid side, whether the key was seen
+    before (a new right-hand side for a resident matrix), the seed of its
+    right-hand side and its arrival time in seconds."""
+    index: int
+    key: int
+    kind: str
+    side: int
+    reuse: bool
+    arrival: float
+
+    @property
+    def solver(self) -> int:
+        return 1 if self.kind == "convdiff" else 0
+
+    def matrix(self) -> "Csr":
+        if self.kind == "poisson":
+            return poisson3d(self.side)
+        if self.kind == "varcoef":
+            return varcoef3d(self.side, seed=self.key, log10_range=SERVE_VARCOEF_RANGE)
+        return convdiff3d(self.side, seed=self.key)[0]
+
+    def rhs(self, seed: int, n: int) -> np.ndarray:
+        return uniform_pm1(seed, STREAM_REQ_RHS + self.index, n)
+
+
+def serving_requests(count: int, seed: int, lo: int = 20, hi: int = 160, rate: float = 0.0,
+                     spd_frac: float = 0.7, reuse_frac: float = 0.2):
+    """A seeded stream of solve requests.  Each request reuses, with
+    probability reuse_frac, the key (and so the matrix) of a uniformly chosen
+    earlier request; otherwise it has a new key, a grid side log-uniform on
+    [lo, hi], and is SPD with probability spd_frac (half 'poisson', half
+    'varcoef') or 'convdiff'.  Arrivals form a Poisson process of the given
+    rate (requests per second; 0: all at time 0)."""
+    sides = serving_sides(count, seed, lo, hi)
+    kind_u = uniform01(seed, STREAM_KIND, count)
+    reuse_u = uniform01(seed, STREAM_REUSE, count)
+    pick_u = uniform01(seed, STREAM_PICK, count)
+    arr_u = uniform01(seed, STREAM_ARRIVAL, count)
+    out = []
+    t = 0.0
+    for i in range(count):
+        if rate > 0:
+            t += -np.log1p(-arr_u[i]) / rate
+        if i > 0 and reuse_u[i] < reuse_frac:
+            src = out[min(int(pick_u[i] * i), i - 1)]
+            out.append(ServeRequest(i, src.key, src.kind, src.side, True, float(t)))
+            continue
+        u = kind_u[i]
+        kind = ("poisson" if u < spd_frac / 2 else "varcoef") if u < spd_frac else "convdiff"
+        out.append(ServeRequest(i, i, kind, int(sides[i]), False, float(t)))
+    return out

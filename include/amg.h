@@ -237,6 +237,71 @@ amg_status amg_batch_free(amg_batch *b);
 amg_status amg_spmv_dot_noalloc(const amg_csr *A, const double *x, double *y, double *dot,
                                 void *stream);
 
+/* Solve server with continuous batching.  The set-up depends only on the
+ * matrix, so one hierarchy serves any number of right-hand sides (Sec. 3,
+ * design principles); the server keeps hierarchies resident on the device
+ * under caller-chosen keys and serves a stream of requests.  Each request is
+ * either a new matrix with a right-hand side (its hierarchy is built, used
+ * and, for a key >= 0, kept) or the key of a resident hierarchy with a new
+ * right-hand side.  Requests wait in a FIFO queue; each of `slots` worker
+ * threads, with its own CUDA stream, admits the first queued request (looking
+ * up to 16 entries ahead) that it can run: a resident key whose hierarchy is
+ * idle, or a new matrix whose estimated device memory fits the HBM budget
+ * after evicting idle resident hierarchies, least recently used first.  A new
+ * matrix larger than the whole budget runs alone.  Admitted requests run
+ * concurrently, so their kernels overlap on the GPU.  Every solve is
+ * deterministic, so a request's result does not depend on what else runs.
+ * Thread-safe: any thread may submit and wait. */
+typedef struct amg_server amg_server;
+
+typedef struct {
+    int slots;          /* concurrent requests (worker threads); <= 0: 4, capped at 64 */
+    int reserved0;
+    int64_t hbm_budget; /* device bytes for resident and in-flight hierarchies;
+                           <= 0: 80% of the free device memory at creation.
+                           A new matrix is charged 72 bytes per nonzero + 64
+                           bytes per row + 8 MiB while its hierarchy is built
+                           and solved, then the hierarchy's own device bytes
+                           while it stays resident. */
+    int64_t reserved[4];
+} amg_server_params;
+
+/* Start a server on the current device.  prm: set-up and solve parameters of
+ * every request (NULL: defaults; the solver field is taken per request).
+ * Errors: INVALID_ARG, CUDA. */
+amg_status amg_server_create(const amg_server_params *sp, const amg_params *prm, amg_server **out);
+
+/* Queue a request and return at once with its id in *id.  key: >= 0 names a
+ * hierarchy kept resident for later requests, < 0 builds a throw-away one.
+ * A: the matrix in host memory (deep-copied), or NULL to reuse the resident
+ * hierarchy of key (the request then fails with INVALID_ARG when it comes up
+ * if the key is not resident).  A key names one matrix: a request that gives
+ * a matrix for a key already resident, or being built, reuses that key's
+ * hierarchy.  f_host: n doubles (copied).  solver:
+ * AMG_SOLVER_CG or AMG_SOLVER_BICGSTAB (for a reused key, the hierarchy's
+ * own).  The initial guess is zero.  Errors: INVALID_ARG. */
+amg_status amg_server_submit(amg_server *s, int64_t key, const amg_csr *A, const double *f_host, int64_t n,
+                             int solver, double rtol, int maxiter, int64_t *id);
+
+/* Block until request id has finished; copy its solution to x_host (n
+ * doubles, may be NULL) and report its iterations, true relative residual,
+ * latency (submit to finish, seconds) and queueing time (submit to
+ * admission); outputs may be NULL.  Returns the request's status (as
+ * amg_setup / amg_solve).  The request is forgotten afterwards: wait once per
+ * id.  An unknown id gives INVALID_ARG. */
+amg_status amg_server_wait(amg_server *s, int64_t id, double *x_host, int *iters, double *relres,
+                           double *latency_s, double *queue_s);
+
+/* Counters: requests finished, resident hierarchies and their device bytes,
+ * the peak of the bytes charged against the budget, and evictions.  Outputs
+ * may be NULL. */
+amg_status amg_server_stats(amg_server *s, int64_t *completed, int *resident_count, int64_t *resident_bytes,
+                            int64_t *peak_bytes, int64_t *evictions);
+
+/* Finish every queued request, stop the workers and free the resident
+ * hierarchies.  Results not yet collected are dropped.  NULL is accepted. */
+amg_status amg_server_destroy(amg_server *s);
+
 /* Kernel classes reported by amg_solve_profile. */
 typedef enum {
     AMG_KC_SPMV_DOT = 0,      /* q = A p with p.q (a1) */

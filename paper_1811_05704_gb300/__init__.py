@@ -87,6 +87,12 @@ _sigs = {
     "amg_batch_tune": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_I)],
     "amg_batch_info": [_VP, C.POINTER(_I64), _VP, _VP],
     "amg_batch_free": [_VP],
+    "amg_server_create": [_VP, C.POINTER(amg_params), C.POINTER(_VP)],
+    "amg_server_submit": [_VP, _I64, C.POINTER(amg_csr), _VP, _I64, _I, _D, _I, C.POINTER(_I64)],
+    "amg_server_wait": [_VP, _I64, _VP, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)],
+    "amg_server_stats": [_VP, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I64), C.POINTER(_I64),
+                         C.POINTER(_I64)],
+    "amg_server_destroy": [_VP],
 }
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
@@ -299,6 +305,57 @@ def amg_batch_tune(b, f, x, rtol=1e-8, maxiter=500):
 
 def amg_batch_free(b):
     _check(_lib.amg_batch_free(b), "amg_batch_free")
+
+
+# ---------------------------------------------------------------- serving
+class amg_server_params(C.Structure):
+    _fields_ = [
+        ("slots", C.c_int),
+        ("reserved0", C.c_int),
+        ("hbm_budget", C.c_int64),
+        ("reserved", C.c_int64 * 4),
+    ]
+
+
+def amg_server_create(slots=4, hbm_budget=0, params: amg_params = None):
+    sp = amg_server_params(slots=slots, hbm_budget=hbm_budget)
+    h = C.c_void_p()
+    p = C.byref(params) if params is not None else None
+    _check(_lib.amg_server_create(C.byref(sp), p, C.byref(h)), "amg_server_create")
+    return h
+
+
+def amg_server_submit(s, key, csr, f_host, solver=AMG_SOLVER_CG, rtol=1e-8, maxiter=500):
+    """csr: amg_csr over host arrays, or None to reuse key's resident
+    hierarchy.  f_host: float64 numpy array (copied).  Returns the request id."""
+    f = np.ascontiguousarray(f_host, dtype=np.float64)
+    rid = C.c_int64()
+    c = C.byref(csr) if csr is not None else None
+    _check(_lib.amg_server_submit(s, key, c, f.ctypes.data, f.size, solver, rtol, maxiter, C.byref(rid)),
+           "amg_server_submit")
+    return rid.value
+
+
+def amg_server_wait(s, rid, n):
+    """Returns (status, x, iters, relres, latency_s, queue_s); blocks until
+    the request has finished (releases the GIL meanwhile)."""
+    x = np.zeros(n, np.float64)
+    it, rr, lat, q = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+    st = _lib.amg_server_wait(s, rid, x.ctypes.data, C.byref(it), C.byref(rr), C.byref(lat), C.byref(q))
+    return st, x, it.value, rr.value, lat.value, q.value
+
+
+def amg_server_stats(s):
+    """Returns dict(completed, resident_count, resident_bytes, peak_bytes, evictions)."""
+    c, rc, rb, pk, ev = C.c_int64(), C.c_int(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.amg_server_stats(s, C.byref(c), C.byref(rc), C.byref(rb), C.byref(pk), C.byref(ev)),
+           "amg_server_stats")
+    return dict(completed=c.value, resident_count=rc.value, resident_bytes=rb.value, peak_bytes=pk.value,
+                evictions=ev.value)
+
+
+def amg_server_destroy(s):
+    _check(_lib.amg_server_destroy(s), "amg_server_destroy")
 
 
 # ------------------------------------------------------------- convenience

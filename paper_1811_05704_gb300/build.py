@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["spmv.cu", "spgemm.cu", "solver.cu", "capi.cu", "noalloc.cu", "tail.cu", "batch.cu"]
-CPP_SOURCES = ["setup_host.cpp", "batch_host.cpp"]
+CPP_SOURCES = ["setup_host.cpp", "batch_host.cpp", "server.cpp"]
 
 
 def _cuda_home():

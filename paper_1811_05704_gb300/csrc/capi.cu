@@ -16,6 +16,10 @@ namespace amg {
 
 static thread_local std::string g_last_error;
 
+// the calling thread's message of amg_last_error (the server reports its
+// requests' errors to the thread that waits for them)
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 void fail(amg_status st, const std::string& msg) { throw Error{st, msg}; }
 
 void cuda_check(cudaError_t e, const char* what) {
@@ -211,6 +215,7 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             auto vec = [&](double*& v) {  // padded: see kPad
                 v = dev_alloc<double>(h->n + kPad);
                 h->dev_allocs.push_back(v);
+                h->dev_bytes += (h->n + kPad) * 8;
                 AMG_CUDA(cudaMemset(v, 0, (h->n + kPad) * sizeof(double)));
             };
             for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->rh, &h->v, &h->ph, &h->sv, &h->sh,
@@ -227,12 +232,15 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             std::memset(h->st_out, 0, sizeof(KState));
             h->stride = std::max(std::max<int>(h->lev[0].A.nblk, vec_grid(h->n)),
                                  stream_grid(std::max(1, h->lev[0].A.ntiles)));
+            h->dev_bytes += 2 * (int64_t)h->stride * 8 + 512;
             h->partial = dev_alloc<double>(2 * (size_t)h->stride);
             h->dev_allocs.push_back(h->partial);
             h->counter = dev_alloc<unsigned int>(1);
             h->dev_allocs.push_back(h->counter);
             AMG_CUDA(cudaMemset(h->counter, 0, sizeof(unsigned int)));
-            AMG_CUDA(cudaDeviceSynchronize());
+            // the set-up's own work only: other streams may be solving meanwhile
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+            AMG_CUDA(cudaStreamSynchronize(nullptr));
         } catch (...) {
             free_handle(h);
             throw;

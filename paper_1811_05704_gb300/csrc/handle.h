@@ -72,6 +72,7 @@ struct amg_handle {
     int stride = 0;
     unsigned int* counter = nullptr;
     std::vector<void*> dev_allocs;
+    int64_t dev_bytes = 0;            // bytes of device memory held (for admission control)
     std::vector<amg::CachedGraph> graphs;
     bool graph_unsupported = false;
     int64_t last_launches = 0;

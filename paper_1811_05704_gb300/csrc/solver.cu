@@ -19,6 +19,7 @@ template <typename T>
 static T* halloc(amg_handle* h, size_t count) {
     T* p = dev_alloc<T>(count > 0 ? count : 1);
     h->dev_allocs.push_back(p);
+    h->dev_bytes += (int64_t)(count > 0 ? count : 1) * (int64_t)sizeof(T);
     return p;
 }
 
@@ -26,6 +27,7 @@ static void track(amg_handle* h, const DevCsr& D) {
     h->dev_allocs.push_back(D.ptr);
     h->dev_allocs.push_back(D.col);
     h->dev_allocs.push_back(D.val);
+    h->dev_bytes += (int64_t)(D.nrows + 1 + kPad) * 4 + (D.nnz + kPad) * 12;
 }
 
 static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, int rows_cap_max) {

@@ -3,7 +3,10 @@
 //
 // Row i of C is accumulated in a hash table in shared memory: a warp per row
 // (table of kWarpSlots) while the row has at most kWarpSlots/2 distinct
-// columns, else a block per row (table of kBlockSlots).  The symbolic pass
+// columns, else a block per row (table of kBlockSlots) while it has at most
+// kBlockSlots/2; wider rows (the dense coarse levels of problems with strong
+// coefficient jumps) go to a block with a dense accumulator of all columns in
+// global memory (L2-resident at the sizes where it occurs).  The symbolic pass
 // counts distinct columns exactly; the numeric pass accumulates
 //     c_ij = ((0 + a_ik1 b_k1j) + a_ik2 b_k2j) + ...
 // over the nonzeros of row i of A in ascending k, with explicit
@@ -14,6 +17,8 @@
 // rank sort before they are written.  Numerical zeros are kept (the pattern is
 // structural).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "amg_internal.h"
 
@@ -48,7 +53,7 @@ __device__ __forceinline__ int insert(int* keys, unsigned mask, int key, bool& a
     return -1;
 }
 
-// error bits: 1 = table overflow (probe failed), 2 = row too wide, 4 = nnz overflow
+// error bits: 1 = table overflow (probe failed), 4 = nnz overflow
 
 // ------------------------------------------------------------- symbolic
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -91,29 +96,98 @@ k_sym_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
 __global__ void __launch_bounds__(kBlockThreads)
 k_sym_block(const int32_t* __restrict__ rows, const int32_t* __restrict__ ap,
             const int32_t* __restrict__ ac, const int32_t* __restrict__ bp,
-            const int32_t* __restrict__ bc, int32_t* __restrict__ count, int* __restrict__ err) {
+            const int32_t* __restrict__ bc, int32_t* __restrict__ count,
+            int32_t* __restrict__ wide, int32_t* __restrict__ nwide) {
     extern __shared__ int smem[];
     int* tab = smem;
-    __shared__ int distinct;
+    __shared__ int distinct, full;
     const int row = rows[blockIdx.x];
     for (int i = threadIdx.x; i < kBlockSlots; i += kBlockThreads) tab[i] = kEmpty;
-    if (threadIdx.x == 0) distinct = 0;
+    if (threadIdx.x == 0) { distinct = 0; full = 0; }
     __syncthreads();
     for (int ka = ap[row]; ka < ap[row + 1]; ++ka) {
         const int k = ac[ka];
         for (int kb = bp[k] + threadIdx.x; kb < bp[k + 1]; kb += kBlockThreads) {
             bool added = false;
-            if (insert(tab, kBlockSlots - 1, bc[kb], added) < 0) atomicOr(err, 1);
+            if (insert(tab, kBlockSlots - 1, bc[kb], added) < 0) full = 1;  // table full: a wide row
             if (added) atomicAdd(&distinct, 1);
         }
         __syncthreads();
-        const int seen = distinct;
+        const bool stop = distinct > kBlockCap || full;
         __syncthreads();  // every thread has read `distinct` before the next step adds to it
-        if (seen > kBlockCap) break;
+        if (stop) break;
     }
     if (threadIdx.x == 0) {
-        if (distinct > kBlockCap) atomicOr(err, 2);
-        count[row] = distinct;
+        if (distinct > kBlockCap || full) {
+            count[row] = -1;
+            wide[atomicAdd(nwide, 1)] = row;
+        } else {
+            count[row] = distinct;
+        }
+    }
+}
+
+// Sum of v over the block (blockDim.x a multiple of 32, at most 1024); the
+// total in every thread.
+__device__ __forceinline__ int block_sum_int(int v, int* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    return t;
+}
+
+// Exclusive prefix of v over the block in thread order; *total gets the sum.
+__device__ __forceinline__ int block_excl_scan_int(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < warp) before += sh[w];
+        all += sh[w];
+    }
+    *total = all;
+    return before + x - v;
+}
+
+// Wide rows, symbolic: a block per row (grid-stride over the wide rows) marks
+// the columns it meets in a bit set of all ncols columns (per block, zero on
+// entry and left zero), then counts them.
+__global__ void __launch_bounds__(kBlockThreads)
+k_sym_wide(int32_t nwide, const int32_t* __restrict__ rows, const int32_t* __restrict__ ap,
+           const int32_t* __restrict__ ac, const int32_t* __restrict__ bp,
+           const int32_t* __restrict__ bc, unsigned* __restrict__ scratch, int64_t words,
+           int32_t* __restrict__ count) {
+    __shared__ int sh[kBlockThreads / 32];
+    unsigned* mark = scratch + (int64_t)blockIdx.x * words;
+    for (int w = blockIdx.x; w < nwide; w += gridDim.x) {
+        const int row = rows[w];
+        for (int ka = ap[row]; ka < ap[row + 1]; ++ka) {
+            const int k = ac[ka];
+            for (int kb = bp[k] + threadIdx.x; kb < bp[k + 1]; kb += kBlockThreads) {
+                const int c = bc[kb];
+                atomicOr(mark + (c >> 5), 1u << (c & 31));
+            }
+        }
+        __syncthreads();
+        int local = 0;
+        for (int64_t i = threadIdx.x; i < words; i += kBlockThreads) {
+            local += __popc(mark[i]);
+            mark[i] = 0u;
+        }
+        const int total = block_sum_int(local, sh);
+        if (threadIdx.x == 0) count[row] = total;
+        __syncthreads();
     }
 }
 
@@ -214,6 +288,7 @@ k_num_block(const int32_t* __restrict__ rows, const int32_t* __restrict__ ap,
     int* lst = keys + kBlockSlots;  // kBlockCap entries
     __shared__ int wbase[kBlockThreads / 32 + 1];
     const int row = rows[blockIdx.x];
+    if (cp[row + 1] - cp[row] > kBlockCap) return;  // a wide row: handled by k_num_wide
     for (int i = threadIdx.x; i < kBlockSlots; i += kBlockThreads) { keys[i] = kEmpty; vals[i] = 0.0; }
     __syncthreads();
     for (int ka = ap[row]; ka < ap[row + 1]; ++ka) {
@@ -260,6 +335,59 @@ k_num_block(const int32_t* __restrict__ rows, const int32_t* __restrict__ ap,
     }
 }
 
+// Wide rows, numeric: the products of step k (one row of B, distinct
+// columns) go straight to a dense accumulator of all ncols columns, steps
+// ordered by a block barrier, so every entry sums its products in ascending
+// k exactly as the hash kernels do.  The occupied columns are then written in
+// ascending order (a scan over the bit set) and the accumulator and the bit
+// set are cleared for the next row.
+__global__ void __launch_bounds__(kBlockThreads)
+k_num_wide(int32_t nwide, const int32_t* __restrict__ rows, const int32_t* __restrict__ ap,
+           const int32_t* __restrict__ ac, const double* __restrict__ av,
+           const int32_t* __restrict__ bp, const int32_t* __restrict__ bc,
+           const double* __restrict__ bv, double* __restrict__ acc_scratch,
+           unsigned* __restrict__ mark_scratch, int32_t ncols, int64_t words,
+           const int32_t* __restrict__ cp, int32_t* __restrict__ cc, double* __restrict__ cv,
+           int* __restrict__ err) {
+    __shared__ int sh[kBlockThreads / 32];
+    double* acc = acc_scratch + (int64_t)blockIdx.x * ncols;
+    unsigned* mark = mark_scratch + (int64_t)blockIdx.x * words;
+    for (int w = blockIdx.x; w < nwide; w += gridDim.x) {
+        const int row = rows[w];
+        for (int ka = ap[row]; ka < ap[row + 1]; ++ka) {
+            const int k = ac[ka];
+            const double a = av[ka];
+            for (int kb = bp[k] + threadIdx.x; kb < bp[k + 1]; kb += kBlockThreads) {
+                const int c = bc[kb];
+                acc[c] = __dadd_rn(acc[c], __dmul_rn(a, bv[kb]));
+                atomicOr(mark + (c >> 5), 1u << (c & 31));
+            }
+            __syncthreads();
+        }
+        const int out0 = cp[row], width = cp[row + 1] - cp[row];
+        int written = 0;
+        for (int64_t base = 0; base < words; base += kBlockThreads) {
+            const int64_t i = base + threadIdx.x;
+            const unsigned m = (i < words) ? mark[i] : 0u;
+            int chunk = 0;
+            int pos = written + block_excl_scan_int(__popc(m), sh, &chunk);
+            for (unsigned bits = m; bits; bits &= bits - 1u) {
+                const int c = (int)(i * 32) + __ffs(bits) - 1;
+                if (pos < width) {
+                    cc[out0 + pos] = c;
+                    cv[out0 + pos] = acc[c];
+                }
+                acc[c] = 0.0;
+                ++pos;
+            }
+            if (i < words) mark[i] = 0u;
+            written += chunk;
+        }
+        if (threadIdx.x == 0 && written != width) atomicOr(err, 1);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) {
@@ -268,9 +396,10 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     C.ncols = B.ncols;
     int32_t* count = dev_alloc<int32_t>(m > 0 ? m : 1);
     int32_t* big = dev_alloc<int32_t>(m > 0 ? m : 1);
-    int32_t* nbig = dev_alloc<int32_t>(1);
+    int32_t* nbig = dev_alloc<int32_t>(2);  // [0]: rows for the block kernels, [1]: wide rows
+    int32_t* wide = dev_alloc<int32_t>(m > 0 ? m : 1);
     int* err = dev_alloc<int>(1);
-    AMG_CUDA(cudaMemsetAsync(nbig, 0, sizeof(int32_t), s));
+    AMG_CUDA(cudaMemsetAsync(nbig, 0, 2 * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     C.ptr = dev_alloc<int32_t>(m + 1 + kPad);
     AMG_CUDA(cudaMemsetAsync(C.ptr, 0, (m + 1 + kPad) * sizeof(int32_t), s));
@@ -291,8 +420,32 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     if (hbig > 0) {
         AMG_CUDA(cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sym_smem));
-        k_sym_block<<<hbig, kBlockThreads, sym_smem, s>>>(big, A.ptr, A.col, B.ptr, B.col, count, err);
+        k_sym_block<<<hbig, kBlockThreads, sym_smem, s>>>(big, A.ptr, A.col, B.ptr, B.col, count, wide,
+                                                          nbig + 1);
         AMG_CUDA(cudaGetLastError());
+    }
+    // wide rows: a dense bit set (symbolic) and accumulator (numeric) per block
+    int32_t hwide = 0;
+    if (hbig > 0) {
+        AMG_CUDA(cudaMemcpyAsync(&hwide, nbig + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+    }
+    const int64_t words = ((int64_t)C.ncols + 31) / 32;
+    int wgrid_wide = 0;
+    if (hwide > 0) {
+        int dev = 0, sms = 0;
+        AMG_CUDA(cudaGetDevice(&dev));
+        AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t per_block = (int64_t)C.ncols * 8 + words * 4;
+        const int64_t cap = std::max<int64_t>(1, (int64_t(1) << 30) / per_block);  // <= 1 GiB of scratch
+        wgrid_wide = (int)std::min<int64_t>(std::min<int64_t>(hwide, 2 * (int64_t)sms), cap);
+        unsigned* mark = dev_alloc<unsigned>((size_t)(wgrid_wide * words));
+        AMG_CUDA(cudaMemsetAsync(mark, 0, (size_t)(wgrid_wide * words) * sizeof(unsigned), s));
+        k_sym_wide<<<wgrid_wide, kBlockThreads, 0, s>>>(hwide, wide, A.ptr, A.col, B.ptr, B.col, mark, words,
+                                                        count);
+        AMG_CUDA(cudaGetLastError());
+        AMG_CUDA(cudaStreamSynchronize(s));
+        dev_free(mark);
     }
     k_scan<<<1, 1024, 0, s>>>(m, count, C.ptr, err);
     AMG_CUDA(cudaGetLastError());
@@ -301,13 +454,13 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     AMG_CUDA(cudaMemcpyAsync(&nnz, C.ptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaStreamSynchronize(s));
-    auto cleanup = [&]() { dev_free(count); dev_free(big); dev_free(nbig); dev_free(err); };
+    auto cleanup = [&]() { dev_free(count); dev_free(big); dev_free(nbig); dev_free(wide); dev_free(err); };
     if (herr) {
         cleanup();
         dev_free(C.ptr);
         C.ptr = nullptr;
         if (herr & 4) fail(AMG_ERR_TOO_LARGE, "Galerkin product has more than 2^31 nonzeros");
-        fail(AMG_ERR_TOO_LARGE, "Galerkin product row wider than 4096 columns");
+        fail(AMG_ERR_CUDA, "sparse product symbolic phase: hash table overflow");
     }
     C.nnz = nnz;
     C.col = dev_alloc<int32_t>(nnz + kPad);
@@ -328,9 +481,23 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
                                                                 B.col, B.val, C.ptr, C.col, C.val, err);
         AMG_CUDA(cudaGetLastError());
     }
+    double* acc = nullptr;
+    unsigned* mark = nullptr;
+    if (hwide > 0) {
+        acc = dev_alloc<double>((size_t)wgrid_wide * C.ncols);
+        mark = dev_alloc<unsigned>((size_t)(wgrid_wide * words));
+        AMG_CUDA(cudaMemsetAsync(acc, 0, (size_t)wgrid_wide * C.ncols * sizeof(double), s));
+        AMG_CUDA(cudaMemsetAsync(mark, 0, (size_t)(wgrid_wide * words) * sizeof(unsigned), s));
+        k_num_wide<<<wgrid_wide, kBlockThreads, 0, s>>>(hwide, wide, A.ptr, A.col, A.val, B.ptr, B.col, B.val,
+                                                        acc, mark, (int32_t)C.ncols, words, C.ptr, C.col,
+                                                        C.val, err);
+        AMG_CUDA(cudaGetLastError());
+    }
     AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaStreamSynchronize(s));
     cleanup();
+    if (acc) dev_free(acc);
+    if (mark) dev_free(mark);
     if (herr) fail(AMG_ERR_CUDA, "sparse product numeric phase inconsistent with its symbolic phase");
 }
 

@@ -17,6 +17,8 @@
 //   spmv+dot             q = A p, p.q                 (Krylov product)
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 
 #include "amg_internal.h"
@@ -343,18 +345,22 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
 }
 
-static int g_sm_count = 0;
-static bool g_pdl = true;
+static std::atomic<int> g_sm_count{0};
+// set by the thread that issues the launches (several host threads may each
+// drive a solve on their own stream)
+static thread_local bool g_pdl = true;
 
 void set_stream_options(bool pdl) { g_pdl = pdl; }
 
 int stream_grid(int ntiles) {
-    if (g_sm_count == 0) {
+    int sms = g_sm_count.load();
+    if (sms == 0) {
         int dev = 0;
         AMG_CUDA(cudaGetDevice(&dev));
-        AMG_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+        AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        g_sm_count.store(sms);
     }
-    return std::max(1, std::min(ntiles, kCtasPerSm * g_sm_count));
+    return std::max(1, std::min(ntiles, kCtasPerSm * sms));
 }
 
 int* dev_err_ptr() {
@@ -380,11 +386,11 @@ static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const 
     const int grid = stream_grid(A.ntiles);
     if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
     const size_t smem = StreamLayout<VT, RMAX, Epi::nvec>::total;
-    static bool configured = false;  // once per template instance
-    if (!configured) {
+    static std::atomic<bool> configured{false};  // once per template instance
+    if (!configured.load()) {
         AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        configured = true;
+        configured.store(true);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

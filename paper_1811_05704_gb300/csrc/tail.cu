@@ -110,15 +110,15 @@ k_tail(const TailPhase* __restrict__ phases, int nph, unsigned int* bar, int* er
 
 template <typename VT, typename T>
 static void launch_tail_t(const TailPlan& plan, const int* skip, cudaStream_t s) {
-    static int per_sm = 0;  // once per template instance
-    static int sms = 0;
-    if (per_sm == 0) {
-        int dev = 0;
+    // once per template instance (thread-safe static initialisation)
+    static const int2 occ = [] {
+        int dev = 0, sm_count = 0, blocks = 0;
         AMG_CUDA(cudaGetDevice(&dev));
-        AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail<VT, T>, 256, 0));
-        per_sm = std::max(1, std::min(per_sm, 4));
-    }
+        AMG_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_tail<VT, T>, 256, 0));
+        return make_int2(std::max(1, std::min(blocks, 4)), sm_count);
+    }();
+    const int per_sm = occ.x, sms = occ.y;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(per_sm * sms);
     cfg.blockDim = dim3(256);

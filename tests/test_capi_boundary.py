@@ -50,8 +50,9 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "amg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(amg_params), sizeof(amg_csr),
-         offsetof(amg_params, use_graph), offsetof(amg_csr, on_device), offsetof(amg_params, jacobi_omega));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(amg_params), sizeof(amg_csr),
+         offsetof(amg_params, use_graph), offsetof(amg_csr, on_device), offsetof(amg_params, jacobi_omega),
+         sizeof(amg_server_params), offsetof(amg_server_params, hbm_budget));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -63,7 +64,8 @@ int main(void) {
     got = list(map(int, out))
     assert got == [ctypes.sizeof(lib.amg_params), ctypes.sizeof(lib.amg_csr),
                    lib.amg_params.use_graph.offset, lib.amg_csr.on_device.offset,
-                   lib.amg_params.jacobi_omega.offset]
+                   lib.amg_params.jacobi_omega.offset, ctypes.sizeof(lib.amg_server_params),
+                   lib.amg_server_params.hbm_budget.offset]
 
 
 def test_params_default(lib):
@@ -81,6 +83,13 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert "null" in lib.amg_last_error()
     assert lib._lib.amg_solve(None, None, None, 1e-8, 10, None, None) == lib.AMG_ERR_INVALID_ARG
     assert lib._lib.amg_free(None) == lib.AMG_OK
+    rid = ctypes.c_int64()
+    f = (ctypes.c_double * 4)()
+    assert lib._lib.amg_server_create(None, None, None) == lib.AMG_ERR_INVALID_ARG
+    assert lib._lib.amg_server_submit(None, 0, None, f, 4, 0, 1e-8, 10, ctypes.byref(rid)) == lib.AMG_ERR_INVALID_ARG
+    assert lib._lib.amg_server_wait(None, 1, None, None, None, None, None) == lib.AMG_ERR_INVALID_ARG
+    assert lib._lib.amg_server_stats(None, None, None, None, None, None) == lib.AMG_ERR_INVALID_ARG
+    assert lib._lib.amg_server_destroy(None) == lib.AMG_OK
 
 
 def test_package_fails_loudly_without_library(lib, tmp_path):

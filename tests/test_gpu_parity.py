@@ -68,6 +68,8 @@ CASES = {
     "poisson2d_101": (lambda: gen.poisson2d_shift(101, 0.05), {"coarse_enough": 100}),
     "spai0_varcoef": (lambda: gen.varcoef3d(16, seed=3), {"smoother": 1, "coarse_enough": 50}),
     "tail_varcoef20": (lambda: gen.varcoef3d(20, seed=1), {"coarse_enough": 40, "use_tail": 1}),
+    # a dense row: Galerkin rows of 3,559 (block hash) and 7,896 (dense accumulator) columns
+    "star40": (lambda: gen.poisson3d_star(40), {}),
 }
 
 

@@ -67,6 +67,13 @@ def test_generators_structure():
     assert abs(np.linalg.norm(v) - 1.0) < 1e-14 and 1.0 <= pe <= 100.0
     # row sums of interior rows vanish (diffusion + upwinding conserve)
     assert np.abs(dc.sum(1)).min() < 1e-12
+    S = gen.poisson3d_star(5, w=0.5)
+    ds = S.to_dense()
+    assert np.array_equal(ds, ds.T) and np.linalg.eigvalsh(ds).min() > 0
+    assert np.count_nonzero(ds[0]) == S.n and all(np.all(np.diff(S.col[S.row_ptr[i]:S.row_ptr[i + 1]]) > 0)
+                                                   for i in range(S.n))
+    # the star adds a graph Laplacian: row sums equal poisson3d's
+    assert np.allclose(ds.sum(1), d.sum(1))
 
 
 # ---------------------------------------------------------------- strength
@@ -330,6 +337,7 @@ def test_restriction_is_transpose(oracle_lib):
     lambda: gen.poisson3d(8),
     lambda: gen.varcoef3d(8, seed=4),
     lambda: gen.convdiff3d(8, seed=4)[0],
+    lambda: gen.poisson3d_star(8),
 ])
 def test_galerkin_equals_dense_triple_product(oracle_lib, maker):
     A = maker()
