@@ -306,7 +306,7 @@ def bench_serving(amg, args):
     """A stream of solve requests through the server: grid sides log-uniform
     on [20, 160] (8,000 to 4,096,000 unknowns), 70% SPD (3D Poisson and
     variable-coefficient diffusion with k = 10^U(-2,2), CG), 30% upwind convection-diffusion
-    (BiCGStab), 20% of the requests a new right-hand side for an earlier
+    (BiCGStab with the SPAI-0 smoother), 20% of the requests a new right-hand side for an earlier
     request's matrix; every request is set up (unless its hierarchy is
     resident) and solved to rtol 1e-8 from host memory.  Saturated
     throughput (all requests queued at once) against the plain API serving
@@ -319,6 +319,10 @@ def bench_serving(amg, args):
     mats = _serve_matrices(reqs)
     gen_s = time.perf_counter() - t0
     A_of = lambda q: mats[(q.kind, q.side)]  # noqa: E731
+    # CG + damped Jacobi for SPD requests; BiCGStab + SPAI-0 for convection-diffusion
+    prm_cg = amg.amg_params_default()
+    prm_bi = amg.amg_params_default(solver=amg.AMG_SOLVER_BICGSTAB, smoother=amg.AMG_SMOOTHER_SPAI0)
+    prm_of = lambda q: prm_bi if q.solver else prm_cg  # noqa: E731
     rhs = [q.rhs(SEED, A_of(q).n) for q in reqs]
     csrs = {c: amg.make_csr(A.n, A.row_ptr, A.col, A.val) for c, A in mats.items()}
     last_use = {q.key: q.index for q in reqs}
@@ -329,7 +333,7 @@ def bench_serving(amg, args):
     t0 = time.perf_counter()
     for q in reqs:
         if q.key not in handles:
-            handles[q.key] = amg.amg_setup(csrs[(q.kind, q.side)], amg.amg_params_default(solver=q.solver))
+            handles[q.key] = amg.amg_setup(csrs[(q.kind, q.side)], prm_of(q))
         x = np.zeros(A_of(q).n)
         serial_status.append(amg.amg_solve_host(handles[q.key], rhs[q.index], x, RTOL, MAXITER)[0])
         if last_use[q.key] == q.index:
@@ -347,7 +351,7 @@ def bench_serving(amg, args):
                 delay = t_start + arrival[q.index] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-            ids.append(amg.amg_server_submit(srv, q.key, csrs[(q.kind, q.side)], rhs[q.index], q.solver,
+            ids.append(amg.amg_server_submit(srv, q.key, csrs[(q.kind, q.side)], rhs[q.index], prm_of(q),
                                              RTOL, MAXITER))
         res = [amg.amg_server_wait(srv, rid, A_of(q).n) for q, rid in zip(reqs, ids)]
         wall = time.perf_counter() - t_start
@@ -492,23 +496,30 @@ def main():
     # ---- mixed precision form (float32 V-cycle under FP64 CG), same workload
     mixed = None
     if not args.no_mixed:
-        S32 = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=amg.AMG_PRECISION_FP32)
-        for _ in range(2):
-            x.zero_()
-            S32.solve(ft, x, RTOL, MAXITER)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(3, args.steps // 2)
-        e0.record(stream)
-        for _ in range(reps):
-            x.zero_()
-            st32, it32, rr32 = S32.solve(ft, x, RTOL, MAXITER)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t32 = e0.elapsed_time(e1) / 1e3 / reps
-        mixed = {"value": 1.0 / t32, "unit": "solves/s", "solve_s": t32, "iterations": it32,
-                 "relres": rr32, "status": st32, "precision": "fp32 V-cycle, fp64 CG"}
-        S32.close()
+        x64 = x.clone()  # the FP64 solution of the timed region
+        mixed = {}
+        for name, prec, desc in (("fp32", amg.AMG_PRECISION_FP32, "fp32 V-cycle, fp64 CG"),
+                                 ("bf16", amg.AMG_PRECISION_BF16,
+                                  "fp32 V-cycle with bf16-stored matrix values, fp64 CG")):
+            S32 = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=prec)
+            for _ in range(2):
+                x.zero_()
+                S32.solve(ft, x, RTOL, MAXITER)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(3, args.steps // 2)
+            e0.record(stream)
+            for _ in range(reps):
+                x.zero_()
+                st32, it32, rr32 = S32.solve(ft, x, RTOL, MAXITER)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t32 = e0.elapsed_time(e1) / 1e3 / reps
+            err = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+            mixed[name] = {"value": 1.0 / t32, "unit": "solves/s", "solve_s": t32, "iterations": it32,
+                           "relres": rr32, "status": st32, "precision": desc, "rel_diff_vs_fp64_x": err,
+                           "speedup_vs_fp64": solve_s / t32}
+            S32.close()
 
     batched = None
     if not args.no_batch:

@@ -55,8 +55,14 @@ typedef enum { AMG_SOLVER_CG = 0, AMG_SOLVER_BICGSTAB = 1 } amg_solver;
 /* FP64: hierarchy and V-cycle in float64.  FP32: the V-cycle (level
  * matrices, smoother diagonals, level vectors) in float32 with float32
  * accumulation, the outer Krylov vectors, dot products, the fine-level
- * operator and the coarsest solve in float64. */
-typedef enum { AMG_PRECISION_FP64 = 0, AMG_PRECISION_FP32 = 1 } amg_precision;
+ * operator and the coarsest solve in float64.  BF16: as FP32, but the
+ * V-cycle's matrix values (A_l, the smoother-scaled A_l of the first
+ * pre-sweep, P_l and R_l) are stored in bfloat16 (each the float64 value
+ * rounded once, to nearest) and widened to float32 as they are used; 6 bytes
+ * per nonzero instead of 8.  FP32 and BF16 need npre = npost = 1; BF16 is
+ * not available to the batched form and does not use the cooperative tail
+ * (use_tail is ignored). */
+typedef enum { AMG_PRECISION_FP64 = 0, AMG_PRECISION_FP32 = 1, AMG_PRECISION_BF16 = 2 } amg_precision;
 
 #define AMG_MAX_LEVELS 32
 
@@ -266,8 +272,8 @@ typedef struct {
     int64_t reserved[4];
 } amg_server_params;
 
-/* Start a server on the current device.  prm: set-up and solve parameters of
- * every request (NULL: defaults; the solver field is taken per request).
+/* Start a server on the current device.  prm: the set-up and solver
+ * parameters of requests that give none (NULL: amg_params_default).
  * Errors: INVALID_ARG, CUDA. */
 amg_status amg_server_create(const amg_server_params *sp, const amg_params *prm, amg_server **out);
 
@@ -277,11 +283,13 @@ amg_status amg_server_create(const amg_server_params *sp, const amg_params *prm,
  * hierarchy of key (the request then fails with INVALID_ARG when it comes up
  * if the key is not resident).  A key names one matrix: a request that gives
  * a matrix for a key already resident, or being built, reuses that key's
- * hierarchy.  f_host: n doubles (copied).  solver:
- * AMG_SOLVER_CG or AMG_SOLVER_BICGSTAB (for a reused key, the hierarchy's
- * own).  The initial guess is zero.  Errors: INVALID_ARG. */
+ * hierarchy.  f_host: n doubles (copied).  prm: set-up and solver parameters
+ * (copied; NULL: the server's) of a hierarchy this request builds; a reused
+ * hierarchy keeps the parameters it was built with, solver included.  The
+ * initial guess is zero.  Invalid parameters fail the request when it comes
+ * up.  Errors: INVALID_ARG. */
 amg_status amg_server_submit(amg_server *s, int64_t key, const amg_csr *A, const double *f_host, int64_t n,
-                             int solver, double rtol, int maxiter, int64_t *id);
+                             const amg_params *prm, double rtol, int maxiter, int64_t *id);
 
 /* Block until request id has finished; copy its solution to x_host (n
  * doubles, may be NULL) and report its iterations, true relative residual,

@@ -26,7 +26,7 @@ AMG_OK, AMG_ERR_INVALID_ARG, AMG_ERR_OOM, AMG_ERR_CUDA = 0, 1, 2, 3
 AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_COARSENING_STALLED, AMG_ERR_TOO_LARGE = 4, 5, 6, 7
 AMG_SMOOTHER_JACOBI, AMG_SMOOTHER_SPAI0 = 0, 1
 AMG_SOLVER_CG, AMG_SOLVER_BICGSTAB = 0, 1
-AMG_PRECISION_FP64, AMG_PRECISION_FP32 = 0, 1
+AMG_PRECISION_FP64, AMG_PRECISION_FP32, AMG_PRECISION_BF16 = 0, 1, 2
 AMG_MAX_LEVELS = 32
 KERNEL_CLASSES = ["spmv_dot", "krylov_update", "presmooth_l0", "restrict_l0", "prolong_l0",
                   "postsmooth_l0", "vcycle_coarser", "coarse_solve", "other"]
@@ -88,7 +88,8 @@ _sigs = {
     "amg_batch_info": [_VP, C.POINTER(_I64), _VP, _VP],
     "amg_batch_free": [_VP],
     "amg_server_create": [_VP, C.POINTER(amg_params), C.POINTER(_VP)],
-    "amg_server_submit": [_VP, _I64, C.POINTER(amg_csr), _VP, _I64, _I, _D, _I, C.POINTER(_I64)],
+    "amg_server_submit": [_VP, _I64, C.POINTER(amg_csr), _VP, _I64, C.POINTER(amg_params), _D, _I,
+                          C.POINTER(_I64)],
     "amg_server_wait": [_VP, _I64, _VP, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D)],
     "amg_server_stats": [_VP, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I64), C.POINTER(_I64),
                          C.POINTER(_I64)],
@@ -325,13 +326,16 @@ def amg_server_create(slots=4, hbm_budget=0, params: amg_params = None):
     return h
 
 
-def amg_server_submit(s, key, csr, f_host, solver=AMG_SOLVER_CG, rtol=1e-8, maxiter=500):
+def amg_server_submit(s, key, csr, f_host, params: amg_params = None, rtol=1e-8, maxiter=500):
     """csr: amg_csr over host arrays, or None to reuse key's resident
-    hierarchy.  f_host: float64 numpy array (copied).  Returns the request id."""
+    hierarchy.  f_host: float64 numpy array (copied).  params: parameters of
+    a hierarchy this request builds (None: the server's).  Returns the
+    request id."""
     f = np.ascontiguousarray(f_host, dtype=np.float64)
     rid = C.c_int64()
     c = C.byref(csr) if csr is not None else None
-    _check(_lib.amg_server_submit(s, key, c, f.ctypes.data, f.size, solver, rtol, maxiter, C.byref(rid)),
+    p = C.byref(params) if params is not None else None
+    _check(_lib.amg_server_submit(s, key, c, f.ctypes.data, f.size, p, rtol, maxiter, C.byref(rid)),
            "amg_server_submit")
     return rid.value
 

@@ -75,6 +75,11 @@ struct DevCsr {
     int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R)
     double* vald = nullptr;  // a_ij d_j: values scaled by the smoother diagonal (level A only)
     float* vald32 = nullptr;
+    // bfloat16 copies of val and vald (bit patterns; mixed-precision V-cycle
+    // with bfloat16-stored values), optional; used instead of val32 and
+    // vald32 when present
+    uint16_t* val16 = nullptr;
+    uint16_t* vald16 = nullptr;
 };
 // Device CSR arrays carry kPad readable elements past their end (row_ptr
 // past n + 1, col/val past nnz): the streaming engine copies 16-byte-aligned
@@ -198,6 +203,7 @@ void launch_coarse_solve(const double* inv, int32_t n, const double* f, double* 
 void launch_coarse_solve_f32(const double* inv, int32_t n, const float* f, float* x,
                              const int* skip, cudaStream_t s);
 void launch_copy_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_copy_to_bf16(const double* a, uint16_t* b, int64_t n, cudaStream_t s);
 void launch_validate_csr(int32_t n, int64_t nnz, const int32_t* ptr, int* err, cudaStream_t s);
 
 // Small coarse levels in one cooperative launch (tail.cu).

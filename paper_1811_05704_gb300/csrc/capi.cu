@@ -43,6 +43,7 @@ T* dev_alloc(size_t count) {
 template int32_t* dev_alloc<int32_t>(size_t);
 template double* dev_alloc<double>(size_t);
 template float* dev_alloc<float>(size_t);
+template uint16_t* dev_alloc<uint16_t>(size_t);
 template unsigned int* dev_alloc<unsigned int>(size_t);
 template KState* dev_alloc<KState>(size_t);
 template TailPhase* dev_alloc<TailPhase>(size_t);
@@ -135,9 +136,10 @@ static void check_params(const amg_params& p) {
         fail(AMG_ERR_INVALID_ARG, "max_coarse_dense must be in [1, 16384]");
     if (p.solver != AMG_SOLVER_CG && p.solver != AMG_SOLVER_BICGSTAB)
         fail(AMG_ERR_INVALID_ARG, "unknown solver");
-    if (p.precision != AMG_PRECISION_FP64 && p.precision != AMG_PRECISION_FP32)
+    if (p.precision != AMG_PRECISION_FP64 && p.precision != AMG_PRECISION_FP32 &&
+        p.precision != AMG_PRECISION_BF16)
         fail(AMG_ERR_INVALID_ARG, "unknown precision");
-    if (p.precision == AMG_PRECISION_FP32 && (p.npre != 1 || p.npost != 1))
+    if (p.precision != AMG_PRECISION_FP64 && (p.npre != 1 || p.npost != 1))
         fail(AMG_ERR_INVALID_ARG, "the float32 V-cycle supports npre = npost = 1");
 }
 
@@ -454,6 +456,8 @@ amg_status amg_batch_setup(int nsys, const amg_csr* systems, const amg_params* p
         check_params(p);
         if (p.npre != 1 || p.npost != 1 || p.solver != AMG_SOLVER_CG)
             fail(AMG_ERR_INVALID_ARG, "the batched solve supports CG with one pre- and one post-sweep");
+        if (p.precision == AMG_PRECISION_BF16)
+            fail(AMG_ERR_INVALID_ARG, "the batched solve supports the FP64 and FP32 V-cycles");
         amg_batch* b = new amg_batch();
         try {
             b->prm = p;

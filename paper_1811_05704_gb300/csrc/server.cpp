@@ -42,7 +42,7 @@ struct Request {
     bool has_matrix = false;
     HostCsr A;
     std::vector<double> f, x;
-    int solver = AMG_SOLVER_CG;
+    amg_params prm{};  // set-up and solver parameters of a new hierarchy
     double rtol = 1e-8;
     int maxiter = 500;
     int64_t estimate = 0;  // device bytes if a hierarchy must be built
@@ -66,7 +66,6 @@ struct Resident {
     int64_t bytes = 0;
     bool busy = false;
     double last_used = 0.0;
-    int solver = AMG_SOLVER_CG;
 };
 
 }  // namespace
@@ -214,9 +213,7 @@ void worker(amg_server* s) {
             c.col = r->A.col.data();
             c.val = r->A.val.data();
             c.on_device = 0;
-            amg_params p = s->prm;
-            p.solver = r->solver;
-            status = amg_setup(&c, &p, st, &h);
+            status = amg_setup(&c, &r->prm, st, &h);
             if (status != AMG_OK) err = amg_last_error();
         } else {
             h->stream = st;  // run on this slot's stream
@@ -256,7 +253,6 @@ void worker(amg_server* s) {
                     R.h = h;
                     R.bytes = h->dev_bytes;
                     R.last_used = now_s();
-                    R.solver = r->solver;
                     s->resident[r->key] = R;
                     s->in_use += R.bytes;
                     s->peak = std::max(s->peak, s->in_use);
@@ -306,12 +302,11 @@ amg_status amg_server_create(const amg_server_params* sp, const amg_params* prm,
 }
 
 amg_status amg_server_submit(amg_server* s, int64_t key, const amg_csr* A, const double* f_host, int64_t n,
-                             int solver, double rtol, int maxiter, int64_t* id) {
-    if (!s || !f_host || n < 1 || !id || (solver != AMG_SOLVER_CG && solver != AMG_SOLVER_BICGSTAB))
-        return AMG_ERR_INVALID_ARG;
+                             const amg_params* prm, double rtol, int maxiter, int64_t* id) {
+    if (!s || !f_host || n < 1 || !id || !(rtol >= 0.0) || maxiter < 0) return AMG_ERR_INVALID_ARG;
     auto r = std::make_unique<Request>();
     r->key = key;
-    r->solver = solver;
+    r->prm = prm ? *prm : s->prm;
     r->rtol = rtol;
     r->maxiter = maxiter;
     r->f.assign(f_host, f_host + n);

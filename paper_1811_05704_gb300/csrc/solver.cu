@@ -50,6 +50,12 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
 }
 
 static void make_f32(amg_handle* h, DevCsr& D) {
+    if (h->prm.precision == AMG_PRECISION_BF16) {
+        D.val16 = halloc<uint16_t>(h, D.nnz + kPad);
+        AMG_CUDA(cudaMemset(D.val16, 0, (D.nnz + kPad) * sizeof(uint16_t)));
+        launch_copy_to_bf16(D.val, D.val16, D.nnz, h->stream);
+        return;
+    }
     D.val32 = halloc<float>(h, D.nnz + kPad);
     AMG_CUDA(cudaMemset(D.val32, 0, (D.nnz + kPad) * sizeof(float)));
     launch_copy_to_f32(D.val, D.val32, D.nnz, h->stream);
@@ -99,7 +105,9 @@ constexpr int64_t kTailMaxNnz = 4 << 20;
 static void build_tail(amg_handle* h) {
     const int nl = (int)h->lev.size();
     h->tail_ls = 0;
-    if (!h->prm.use_tail || h->prm.npre != 1 || h->prm.npost != 1 || nl < 3) return;
+    if (!h->prm.use_tail || h->prm.npre != 1 || h->prm.npost != 1 || nl < 3 ||
+        h->prm.precision == AMG_PRECISION_BF16)
+        return;
     int ls = 0;
     for (int l = 1; l < nl - 1; ++l)
         if (h->lev[l].A.nnz <= kTailMaxNnz) { ls = l; break; }
@@ -163,7 +171,7 @@ static void build_tail(amg_handle* h) {
 // error, and so is a coarsest level larger than max_coarse_dense.
 void build_hierarchy(amg_handle* h, HostCsr A) {
     const amg_params& prm = h->prm;
-    const bool f32 = prm.precision == AMG_PRECISION_FP32;
+    const bool f32 = prm.precision != AMG_PRECISION_FP64;  // float32 V-cycle (values fp32 or bf16)
     h->lev.clear();
     h->lev.reserve(AMG_MAX_LEVELS + 1);  // references to levels stay valid below
     h->lev.emplace_back();
@@ -224,9 +232,15 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         }
         if (f32) {
             make_f32(h, L.A);
-            L.A.vald32 = halloc<float>(h, L.A.nnz + kPad);
-            AMG_CUDA(cudaMemset(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float)));
-            launch_copy_to_f32(L.A.vald, L.A.vald32, L.A.nnz, h->stream);
+            if (prm.precision == AMG_PRECISION_BF16) {
+                L.A.vald16 = halloc<uint16_t>(h, L.A.nnz + kPad);
+                AMG_CUDA(cudaMemset(L.A.vald16, 0, (L.A.nnz + kPad) * sizeof(uint16_t)));
+                launch_copy_to_bf16(L.A.vald, L.A.vald16, L.A.nnz, h->stream);
+            } else {
+                L.A.vald32 = halloc<float>(h, L.A.nnz + kPad);
+                AMG_CUDA(cudaMemset(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float)));
+                launch_copy_to_f32(L.A.vald, L.A.vald32, L.A.nnz, h->stream);
+            }
             L.d32 = halloc<float>(h, n + kPad);
             std::vector<float> d32(L.dhost.begin(), L.dhost.end());
             d32.resize(n + kPad, 0.0f);
@@ -418,7 +432,7 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
 
 static void issue_vcycle(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
                          const Reduce* rz) {
-    if (h->prm.precision == AMG_PRECISION_FP32) issue_vcycle32(h, I, r, z, skip, rz);
+    if (h->prm.precision != AMG_PRECISION_FP64) issue_vcycle32(h, I, r, z, skip, rz);
     else issue_vcycle64(h, I, r, z, skip, rz);
 }
 

@@ -15,6 +15,7 @@
 //   postsmooth           y = x + d (f - A x) [, w.y]  (Alg. 2 post-relaxation)
 //   residual             r = f - A x, r.r, f.f
 //   spmv+dot             q = A p, p.q                 (Krylov product)
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -45,10 +46,16 @@ constexpr int kCtasPerSm = 2;
 
 __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 
+// Nonzero spans are copied from a start rounded down, and to an end rounded
+// up, to a multiple of nz_align elements, so that both the column indices and
+// the values start and end on 16-byte boundaries.
+template <typename VT>
+__host__ __device__ constexpr int nz_align() { return sizeof(VT) >= 4 ? 4 : 16 / (int)sizeof(VT); }
+
 template <typename VT, int RMAX, int NV>
 struct StreamLayout {
     static constexpr int rp_n = RMAX + 8;       // row pointers of the tile (+ alignment slack)
-    static constexpr int nz_n = kTileNnz + 8;   // nonzeros of the tile (+ alignment slack)
+    static constexpr int nz_n = kTileNnz + 2 * nz_align<VT>();  // nonzeros of the tile (+ alignment slack)
     static constexpr int vec_n = RMAX + 8;      // row-indexed vector slice, 8-byte slots
     static constexpr size_t rp_bytes = (size_t)rp_n * 4;
     static constexpr size_t col_bytes = (size_t)nz_n * 4;
@@ -166,7 +173,8 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
             auto issue = [&](int i) {
                 const int s = i % kStages;
                 const int ar = cur.x & ~3, re = (nxt.x + 1 + 3) & ~3, vre = (nxt.x + 3) & ~3;
-                const int ak = cur.y & ~3, ke = (nxt.y + 3) & ~3;
+                constexpr int na = nz_align<VT>();
+                const int ak = cur.y & ~(na - 1), ke = (nxt.y + na - 1) & ~(na - 1);
                 info[s] = make_int4(cur.x, nxt.x, ar, ak);
                 const uint32_t brp = (uint32_t)(re - ar) * 4u;
                 const uint32_t bnz = (uint32_t)(ke - ak);
@@ -462,26 +470,37 @@ void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int*
     run(P, P.val, EpiProlong{xc, x}, Reduce{}, skip, s);
 }
 
+static const __nv_bfloat16* bf16_of(const uint16_t* p) { return reinterpret_cast<const __nv_bfloat16*>(p); }
+
+// The float32 V-cycle kernels read bfloat16-stored values when the matrix has
+// them (AMG_PRECISION_BF16), else float32 values.
+template <typename Epi>
+static void run32(const DevCsr& A, const float* v32, const uint16_t* v16, const Epi& epi, const Reduce& red,
+                  const int* skip, cudaStream_t s) {
+    if (v16) run(A, bf16_of(v16), epi, red, skip, s);
+    else run(A, v32, epi, red, skip, s);
+}
+
 void launch_spmv_f32(const DevCsr& A, const float* x, float* y, const int* skip, cudaStream_t s) {
-    run(A, A.val32, EpiY32{x, y}, Reduce{}, skip, s);
+    run32(A, A.val32, A.val16, EpiY32{x, y}, Reduce{}, skip, s);
 }
 
 void launch_presmooth_residual_f32(const DevCsr& A, const float* d, const float* f32,
                                    const double* f64, float* x, float* t, const int* skip,
                                    cudaStream_t s) {
-    run(A, A.vald32, EpiPre32{d, f32, f64, x, t}, Reduce{}, skip, s);
+    run32(A, A.vald32, A.vald16, EpiPre32{d, f32, f64, x, t}, Reduce{}, skip, s);
 }
 
 void launch_smooth_f32(const DevCsr& A, const float* d, const float* f32, const double* f64,
                        const float* x, float* y32, double* y64, const double* w,
                        const Reduce* r, const int* skip, cudaStream_t s) {
-    if (r) run(A, A.val32, EpiSmooth32<true>{d, f32, f64, x, y32, y64, w}, *r, skip, s);
-    else run(A, A.val32, EpiSmooth32<false>{d, f32, f64, x, y32, y64, nullptr}, Reduce{}, skip, s);
+    if (r) run32(A, A.val32, A.val16, EpiSmooth32<true>{d, f32, f64, x, y32, y64, w}, *r, skip, s);
+    else run32(A, A.val32, A.val16, EpiSmooth32<false>{d, f32, f64, x, y32, y64, nullptr}, Reduce{}, skip, s);
 }
 
 void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const int* skip,
                             cudaStream_t s) {
-    run(P, P.val32, EpiProlong32{xc, x}, Reduce{}, skip, s);
+    run32(P, P.val32, P.val16, EpiProlong32{xc, x}, Reduce{}, skip, s);
 }
 
 // Standalone product on a caller's device CSR: uniform row split (no
@@ -635,6 +654,13 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
         b[i] = (float)a[i];
 }
 
+// float64 -> bfloat16, one rounding to nearest even
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __double2bfloat16(a[i]);
+}
+
 // Structure check of a caller's device CSR before the standalone product:
 // bit 0 of *err is set if row_ptr[0] != 0, row_ptr decreases, or
 // row_ptr[n] != nnz.
@@ -704,6 +730,13 @@ void launch_coarse_solve_f32(const double* inv, int32_t n, const float* f, float
                              const int* skip, cudaStream_t s) {
     const int rows_per_block = kThreads / 32;
     k_coarse<float><<<(n + rows_per_block - 1) / rows_per_block, kThreads, 0, s>>>(inv, n, f, x, skip);
+    AMG_CUDA(cudaGetLastError());
+}
+
+void launch_copy_to_bf16(const double* a, uint16_t* b, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535);
+    k_to_bf16<<<grid, 256, 0, s>>>(a, reinterpret_cast<__nv_bfloat16*>(b), n);
     AMG_CUDA(cudaGetLastError());
 }
 

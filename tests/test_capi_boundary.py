@@ -86,10 +86,22 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     rid = ctypes.c_int64()
     f = (ctypes.c_double * 4)()
     assert lib._lib.amg_server_create(None, None, None) == lib.AMG_ERR_INVALID_ARG
-    assert lib._lib.amg_server_submit(None, 0, None, f, 4, 0, 1e-8, 10, ctypes.byref(rid)) == lib.AMG_ERR_INVALID_ARG
+    assert lib._lib.amg_server_submit(None, 0, None, f, 4, None, 1e-8, 10, ctypes.byref(rid)) == lib.AMG_ERR_INVALID_ARG
     assert lib._lib.amg_server_wait(None, 1, None, None, None, None, None) == lib.AMG_ERR_INVALID_ARG
     assert lib._lib.amg_server_stats(None, None, None, None, None, None) == lib.AMG_ERR_INVALID_ARG
     assert lib._lib.amg_server_destroy(None) == lib.AMG_OK
+    # parameter checks run before any device work
+    import numpy as np
+    ptr, col, val = np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.0])
+    csr = lib.make_csr(1, ptr, col, val)
+    for bad in (dict(precision=3), dict(precision=2, npre=2), dict(solver=7), dict(max_levels=0)):
+        assert lib._lib.amg_setup(ctypes.byref(csr), ctypes.byref(lib.amg_params_default(**bad)), None,
+                                  ctypes.byref(h)) == lib.AMG_ERR_INVALID_ARG, bad
+    arr = (lib.amg_csr * 1)(csr)
+    assert lib._lib.amg_batch_setup(1, ctypes.cast(arr, ctypes.c_void_p),
+                                    ctypes.byref(lib.amg_params_default(precision=2)), None,
+                                    ctypes.byref(h)) == lib.AMG_ERR_INVALID_ARG
+    assert "FP64 and FP32" in lib.amg_last_error()
 
 
 def test_package_fails_loudly_without_library(lib, tmp_path):

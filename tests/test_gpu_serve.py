@@ -35,6 +35,14 @@ def _estimate(A):
     return 72 * A.nnz + 64 * A.n + (8 << 20)
 
 
+def _params(amg, q):
+    """CG with damped Jacobi for the SPD requests; BiCGStab with SPAI-0 for
+    the convection-diffusion ones (damped Jacobi stalls at high Peclet)."""
+    if q.solver:
+        return amg.amg_params_default(solver=amg.AMG_SOLVER_BICGSTAB, smoother=amg.AMG_SMOOTHER_SPAI0)
+    return amg.amg_params_default()
+
+
 def _true_relres(A, x, f):
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
     return np.linalg.norm(f - np.bincount(rows, weights=A.val * x[A.col], minlength=A.n)) / np.linalg.norm(f)
@@ -48,8 +56,7 @@ def _alone(amg, reqs, seed):
             mats[q.key] = q.matrix()
         A = mats[q.key]
         if q.key not in handles:
-            handles[q.key] = amg.amg_setup(amg.make_csr(A.n, A.row_ptr, A.col, A.val),
-                                           amg.amg_params_default(solver=q.solver))
+            handles[q.key] = amg.amg_setup(amg.make_csr(A.n, A.row_ptr, A.col, A.val), _params(amg, q))
         f = q.rhs(seed, A.n)
         x = np.zeros(A.n)
         st, it, rr = amg.amg_solve_host(handles[q.key], f, x, RTOL, 300)
@@ -62,7 +69,7 @@ def _alone(amg, reqs, seed):
 def _submit(amg, srv, q, mats, seed, with_matrix=True):
     A = mats[q.key]
     csr = amg.make_csr(A.n, A.row_ptr, A.col, A.val) if with_matrix else None
-    return amg.amg_server_submit(srv, q.key, csr, q.rhs(seed, A.n), q.solver, RTOL, 300)
+    return amg.amg_server_submit(srv, q.key, csr, q.rhs(seed, A.n), _params(amg, q), RTOL, 300)
 
 
 def test_served_results_equal_alone(amg):
@@ -96,7 +103,7 @@ def test_served_results_match_oracle(amg):
         A = mats[q.key]
         f = q.rhs(seed, A.n)
         st, x, it, rr, _, _ = amg.amg_server_wait(srv, rid, A.n)
-        H = oracle.Hierarchy(A)
+        H = oracle.Hierarchy(A, smoother=1 if q.solver else 0)
         xo, ito, rro, sto = (H.bicgstab if q.solver else H.cg)(f, rtol=RTOL, maxiter=300)
         assert st == 0 and sto == 0
         assert _true_relres(A, x, f) <= RTOL and abs(rr - _true_relres(A, x, f)) <= 1e-12
@@ -185,6 +192,7 @@ def test_failing_requests_fail_alone(amg):
     r_diag = amg.amg_server_submit(srv, 2, c(bad_diag), gen.uniform_pm1(seed, 2, bad_diag.n))
     r_nokey = amg.amg_server_submit(srv, 99, None, good)
     r_len = amg.amg_server_submit(srv, 1, None, good[:100])
+    r_prm = amg.amg_server_submit(srv, 4, c(A), good, amg.amg_params_default(npre=99))
     with pytest.raises(amg.AmgError):  # matrix and right-hand side sizes differ
         amg.amg_server_submit(srv, 3, c(A), good[:100])
     r_after = amg.amg_server_submit(srv, 1, None, good)
@@ -195,6 +203,8 @@ def test_failing_requests_fail_alone(amg):
     assert amg.amg_last_error()
     assert amg.amg_server_wait(srv, r_nokey, A.n)[0] == amg.AMG_ERR_INVALID_ARG
     assert amg.amg_server_wait(srv, r_len, 100)[0] == amg.AMG_ERR_INVALID_ARG
+    assert amg.amg_server_wait(srv, r_prm, A.n)[0] == amg.AMG_ERR_INVALID_ARG
+    assert "npre" in amg.amg_last_error()
     st_after = amg.amg_server_wait(srv, r_after, A.n)
     assert st_after[0] == 0 and np.array_equal(st_after[1], st_ok[1])
     assert amg.amg_server_wait(srv, r_after, A.n)[0] == amg.AMG_ERR_INVALID_ARG  # already collected
