@@ -73,6 +73,27 @@ def kernel_bytes(info):
     }
 
 
+# GB300's FP64 vector rate: 1.25 TFLOP/s nominal, i.e. about 4 FP64 flops (two
+# fused multiply-adds) per clock per SM at 152 SMs x 2.07 GHz.  The FP64 CSR
+# kernels do 2 flops per 12 bytes, so at 6.7 TB/s they need 1.1 TFLOP/s: they
+# are bound by HBM and the FP64 pipe together.
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def kernel_flops(info):
+    """FP64 operations per launch of each finest-level kernel (a fused
+    multiply-add counts 2)."""
+    n0, z0 = info["rows"][0], info["nnz"][0]
+    zp = info["nnz_p"][0]
+    return {
+        "spmv_dot": 2 * z0 + 2 * n0,              # A p, p.q
+        "presmooth_l0": 2 * z0 + 2 * n0,          # A (d f) on scaled values, x = d f, t = f - s
+        "restrict_l0": 2 * zp,                    # R t
+        "prolong_l0": 2 * zp + n0,                # x += P x_1
+        "postsmooth_l0": 2 * z0 + 5 * n0,         # A x, f - s, x + d (.), f.y
+    }
+
+
 def bytes_per_iteration(info, coarse_n):
     """Algorithmic bytes of one CG iteration (the kernels the solve launches)."""
     b = 0
@@ -488,9 +509,13 @@ def main():
     avg_ms = ms[dom] / max(1, ln[dom])
     peak, peak_kind = peaks()
     achieved = kb[dom] / (avg_ms / 1e3) / 1e9
+    kf = kernel_flops(info)
+    fp64_gflops = kf[dom] / (avg_ms / 1e3) / 1e9
     traffic = committed_traffic(dom)
     per_kernel = {k: {"launches": ln[k], "ms": round(ms[k], 4),
-                      "gbs": (round(kb[k] * ln[k] / (ms[k] / 1e3) / 1e9, 1) if k in kb and ms[k] > 0 else None)}
+                      "gbs": (round(kb[k] * ln[k] / (ms[k] / 1e3) / 1e9, 1) if k in kb and ms[k] > 0 else None),
+                      "fp64_gflops": (round(kf[k] * ln[k] / (ms[k] / 1e3) / 1e9, 1)
+                                      if k in kf and ms[k] > 0 else None)}
                   for k in ms}
 
     # ---- mixed precision form (float32 V-cycle under FP64 CG), same workload
@@ -551,7 +576,10 @@ def main():
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                      "traffic": traffic, "algorithmic_bytes_per_launch": kb[dom],
                      "avg_launch_ms": avg_ms, "timing": "CUDA events around every launch of an "
-                     "instrumented solve on the same stream, run right after the timed region"},
+                     "instrumented solve on the same stream, run right after the timed region",
+                     "fp64_alu": {"achieved": fp64_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                                  "frac": fp64_gflops / FP64_PEAK_GFLOPS, "flops_per_launch": kf[dom],
+                                  "peak_kind": "nominal (GB300 FP64 1.25 TFLOP/s: 2 FMA/clk/SM at 2.07 GHz)"}},
         "solve_frac_of_peak": solve_gbs / peak,
         "kernels": per_kernel,
         "mixed": mixed,

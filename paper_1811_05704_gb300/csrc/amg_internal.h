@@ -226,8 +226,6 @@ struct TailPhase {
 struct TailPlan {
     TailPhase* phases = nullptr;  // device array
     int nph = 0;
-    unsigned int* bar = nullptr;  // grid barrier state, 2 words
-    int* err = nullptr;           // device error word
 };
 void launch_tail(const TailPlan& plan, bool f32, const int* skip, cudaStream_t s);
 int* dev_err_ptr();

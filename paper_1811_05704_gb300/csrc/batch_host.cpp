@@ -18,6 +18,7 @@
 #include <thread>
 
 #include "batch.h"
+#include "host_parallel.h"
 
 namespace amg {
 
@@ -29,32 +30,6 @@ struct HSys {
     std::vector<double> inv;
     int nc = 0;
 };
-
-template <class F>
-void parallel_for(int n, F&& fn) {
-    const unsigned hw = std::thread::hardware_concurrency();
-    const unsigned nt = std::max(1u, std::min(16u, hw ? hw : 1u));
-    std::atomic<int> next{0};
-    std::exception_ptr err;
-    std::mutex m;
-    auto worker = [&]() {
-        for (;;) {
-            const int i = next++;
-            if (i >= n) break;
-            try {
-                fn(i);
-            } catch (...) {
-                std::lock_guard<std::mutex> g(m);
-                if (!err) err = std::current_exception();
-            }
-        }
-    };
-    std::vector<std::thread> pool;
-    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(worker);
-    worker();
-    for (auto& t : pool) t.join();
-    if (err) std::rethrow_exception(err);
-}
 
 // One level of the setup of one system (the stop rule and steps of
 // Algorithm 1, as in the single-system setup).  Returns true if the system

@@ -1,0 +1,71 @@
+// host_parallel.h -- small host thread helpers for the set-up.
+//
+// Work is split into a fixed number of contiguous chunks that depends only on
+// the problem size, so per-chunk results (partial maxima, row lists) are
+// combined in chunk order and every result is independent of the thread
+// count and of scheduling.
+#pragma once
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <exception>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace amg {
+
+// Host threads for one parallel step (at most 16).
+inline unsigned host_threads() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    return std::max(1u, std::min(16u, hw ? hw : 1u));
+}
+
+// Run fn(i) for i in [0, n) on host_threads() threads; rethrows the first
+// exception after all workers finished.
+template <class F>
+void parallel_for(int64_t n, F&& fn) {
+    const unsigned nt = (unsigned)std::min<int64_t>(host_threads(), std::max<int64_t>(n, 1));
+    std::atomic<int64_t> next{0};
+    std::exception_ptr err;
+    std::mutex m;
+    auto worker = [&]() {
+        for (;;) {
+            const int64_t i = next++;
+            if (i >= n) break;
+            try {
+                fn(i);
+            } catch (...) {
+                std::lock_guard<std::mutex> g(m);
+                if (!err) err = std::current_exception();
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    if (err) std::rethrow_exception(err);
+}
+
+// Number of chunks for n rows: one per 65,536 rows, at most 64, so small
+// matrices (and the many small systems of the batched set-up, which already
+// run one system per thread) stay on the calling thread.
+inline int row_chunks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(64, n / 65536));
+}
+
+// fn(c, lo, hi) for the chunks c of [0, n): chunk c is
+// [n c / C, n (c + 1) / C) with C = row_chunks(n).
+template <class F>
+void parallel_rows(int64_t n, F&& fn) {
+    const int C = row_chunks(n);
+    if (C == 1) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    parallel_for(C, [&](int64_t c) { fn((int)c, n * c / C, n * (c + 1) / C); });
+}
+
+}  // namespace amg

@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "amg_internal.h"
+#include "host_parallel.h"
 
 namespace amg {
 
@@ -22,29 +23,45 @@ void host_validate(const HostCsr& A) {
     if (A.nrows < 1) fail(AMG_ERR_INVALID_ARG, "matrix has no rows");
     if ((int64_t)A.ptr.size() != A.nrows + 1) fail(AMG_ERR_INVALID_ARG, "row_ptr size");
     if (A.ptr[0] != 0) fail(AMG_ERR_INVALID_ARG, "row_ptr[0] != 0");
-    for (int64_t i = 0; i < A.nrows; ++i) {
+    // row_ptr first (the rows below index col and val through it)
+    for (int64_t i = 0; i < A.nrows; ++i)
         if (A.ptr[i + 1] < A.ptr[i]) fail(AMG_ERR_INVALID_ARG, "row_ptr not monotone at row " + std::to_string(i));
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-            if (A.col[k] < 0 || A.col[k] >= A.ncols)
-                fail(AMG_ERR_INVALID_ARG, "column index out of range in row " + std::to_string(i));
-            if (k > A.ptr[i] && A.col[k] <= A.col[k - 1])
-                fail(AMG_ERR_INVALID_ARG, "columns not strictly ascending in row " + std::to_string(i));
-            if (!std::isfinite(A.val[k]))
-                fail(AMG_ERR_INVALID_ARG, "non-finite value in row " + std::to_string(i));
-        }
+    if ((int64_t)A.ptr[A.nrows] > (int64_t)A.col.size() || (int64_t)A.ptr[A.nrows] > (int64_t)A.val.size())
+        fail(AMG_ERR_INVALID_ARG, "row_ptr[n] exceeds the column and value arrays");
+    // the first bad row of each chunk; the lowest over the chunks is reported
+    std::vector<int64_t> bad(row_chunks(A.nrows), -1);
+    std::vector<int> why(bad.size(), 0);
+    parallel_rows(A.nrows, [&](int c, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi && bad[c] < 0; ++i)
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                int w = 0;
+                if (A.col[k] < 0 || A.col[k] >= A.ncols) w = 1;
+                else if (k > A.ptr[i] && A.col[k] <= A.col[k - 1]) w = 2;
+                else if (!std::isfinite(A.val[k])) w = 3;
+                if (w) { bad[c] = i; why[c] = w; break; }
+            }
+    });
+    for (size_t c = 0; c < bad.size(); ++c) {
+        if (bad[c] < 0) continue;
+        const std::string row = std::to_string(bad[c]);
+        if (why[c] == 1) fail(AMG_ERR_INVALID_ARG, "column index out of range in row " + row);
+        if (why[c] == 2) fail(AMG_ERR_INVALID_ARG, "columns not strictly ascending in row " + row);
+        fail(AMG_ERR_INVALID_ARG, "non-finite value in row " + row);
     }
 }
 
 std::vector<double> host_diagonal(const HostCsr& A) {
     std::vector<double> dg(A.nrows, 0.0);
-    for (int64_t i = 0; i < A.nrows; ++i) {
-        const int32_t* b = A.col.data() + A.ptr[i];
-        const int32_t* e = A.col.data() + A.ptr[i + 1];
-        const int32_t* it = std::lower_bound(b, e, (int32_t)i);
-        if (it != e && *it == i) dg[i] = A.val[it - A.col.data()];
-        if (dg[i] == 0.0)
-            fail(AMG_ERR_INVALID_ARG, "zero or missing diagonal in row " + std::to_string(i));
-    }
+    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const int32_t* b = A.col.data() + A.ptr[i];
+            const int32_t* e = A.col.data() + A.ptr[i + 1];
+            const int32_t* it = std::lower_bound(b, e, (int32_t)i);
+            if (it != e && *it == i) dg[i] = A.val[it - A.col.data()];
+        }
+    });
+    for (int64_t i = 0; i < A.nrows; ++i)
+        if (dg[i] == 0.0) fail(AMG_ERR_INVALID_ARG, "zero or missing diagonal in row " + std::to_string(i));
     return dg;
 }
 
@@ -56,12 +73,14 @@ namespace {
 std::vector<uint8_t> strong_mask(const HostCsr& A, const std::vector<double>& dg, double eps) {
     const double e2 = eps * eps;
     std::vector<uint8_t> s(A.nnz(), 0);
-    for (int64_t i = 0; i < A.nrows; ++i)
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-            const int32_t j = A.col[k];
-            const double a = A.val[k];
-            s[k] = (j != i) && (a * a > e2 * std::fabs(dg[i] * dg[j]));
-        }
+    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                const int32_t j = A.col[k];
+                const double a = A.val[k];
+                s[k] = (j != i) && (a * a > e2 * std::fabs(dg[i] * dg[j]));
+            }
+    });
     return s;
 }
 
@@ -82,8 +101,10 @@ int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double e
     int32_t next = 0;
 
     std::vector<int32_t> degree(n, 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) degree[i] += s[k];
+    parallel_rows(n, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) degree[i] += s[k];
+    });
 
     for (int64_t i = 0; i < n; ++i)
         if (degree[i] == 0) agg[i] = next++;
@@ -100,20 +121,23 @@ int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double e
         ++next;
     }
 
+    // pass 2 reads only the assignment after pass 1: rows are independent
     const std::vector<int32_t> after1(agg);
-    for (int64_t i = 0; i < n; ++i) {
-        if (after1[i] != -1) continue;
-        int32_t pick = -1;
-        double best = -1.0;
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-            if (!s[k]) continue;
-            const int32_t j = A.col[k];
-            if (after1[j] == -1) continue;
-            const double c = std::fabs(A.val[k]) / std::sqrt(std::fabs(dg[i] * dg[j]));
-            if (c > best) { best = c; pick = after1[j]; }
+    parallel_rows(n, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            if (after1[i] != -1) continue;
+            int32_t pick = -1;
+            double best = -1.0;
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                if (!s[k]) continue;
+                const int32_t j = A.col[k];
+                if (after1[j] == -1) continue;
+                const double c = std::fabs(A.val[k]) / std::sqrt(std::fabs(dg[i] * dg[j]));
+                if (c > best) { best = c; pick = after1[j]; }
+            }
+            if (pick != -1) agg[i] = pick;
         }
-        if (pick != -1) agg[i] = pick;
-    }
+    });
 
     for (int64_t i = 0; i < n; ++i) {
         if (agg[i] != -1) continue;
@@ -143,57 +167,73 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
 
     std::vector<int64_t> size(nagg, 0);
     for (int64_t i = 0; i < n; ++i) size[agg[i]]++;
-    std::vector<double> t(n);
-    for (int64_t i = 0; i < n; ++i) t[i] = 1.0 / std::sqrt((double)size[agg[i]]);
-
-    std::vector<double> dF(n);
-    for (int64_t i = 0; i < n; ++i) {
-        double weak = 0.0;
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
-            if (A.col[k] != i && !s[k]) weak += A.val[k];
-        dF[i] = dg[i] - weak;
-    }
-    double rho = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        double row = 0.0;
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-            if (A.col[k] == i) row += std::fabs(dF[i]);
-            else if (s[k]) row += std::fabs(A.val[k]);
+    std::vector<double> t(n), dF(n);
+    const int C = row_chunks(n);
+    std::vector<double> rho_c(C, 0.0);  // per-chunk maxima; a max is order-independent
+    parallel_rows(n, [&](int c, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            t[i] = 1.0 / std::sqrt((double)size[agg[i]]);
+            double weak = 0.0;
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+                if (A.col[k] != i && !s[k]) weak += A.val[k];
+            dF[i] = dg[i] - weak;
         }
-        rho = std::max(rho, row / std::fabs(dF[i]));
-    }
+        for (int64_t i = lo; i < hi; ++i) {
+            double row = 0.0;
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                if (A.col[k] == i) row += std::fabs(dF[i]);
+                else if (s[k]) row += std::fabs(A.val[k]);
+            }
+            rho_c[c] = std::max(rho_c[c], row / std::fabs(dF[i]));
+        }
+    });
+    double rho = 0.0;
+    for (double r : rho_c) rho = std::max(rho, r);
     omega = (4.0 / 3.0) / rho;
 
+    // rows of P per chunk, then concatenated in chunk order
+    std::vector<std::vector<int32_t>> ccol(C);
+    std::vector<std::vector<double>> cval(C);
     P.nrows = n;
     P.ncols = nagg;
     P.ptr.assign(n + 1, 0);
-    P.col.clear();
-    P.val.clear();
-    P.col.reserve(A.nnz() + n);
-    P.val.reserve(A.nnz() + n);
-    std::vector<std::pair<int32_t, double>> row;  // (coarse column, s_ij), few entries
-    for (int64_t i = 0; i < n; ++i) {
-        row.clear();
-        row.emplace_back(agg[i], 0.0);
-        for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-            const int32_t j = A.col[k];
-            if (j != i && !s[k]) continue;
-            const double a = (j == i) ? dF[i] : A.val[k];
-            const int32_t c = agg[j];
-            auto it = std::find_if(row.begin(), row.end(),
-                                   [c](const std::pair<int32_t, double>& e) { return e.first == c; });
-            if (it == row.end()) it = row.emplace(row.end(), c, 0.0);
-            it->second += a * t[j];
+    parallel_rows(n, [&](int c, int64_t lo, int64_t hi) {
+        std::vector<std::pair<int32_t, double>> row;  // (coarse column, s_ij), few entries
+        std::vector<int32_t>& oc = ccol[c];
+        std::vector<double>& ov = cval[c];
+        oc.reserve(A.ptr[hi] - A.ptr[lo] + (hi - lo));
+        ov.reserve(A.ptr[hi] - A.ptr[lo] + (hi - lo));
+        for (int64_t i = lo; i < hi; ++i) {
+            row.clear();
+            row.emplace_back(agg[i], 0.0);
+            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                const int32_t j = A.col[k];
+                if (j != i && !s[k]) continue;
+                const double a = (j == i) ? dF[i] : A.val[k];
+                const int32_t cc = agg[j];
+                auto it = std::find_if(row.begin(), row.end(),
+                                       [cc](const std::pair<int32_t, double>& e) { return e.first == cc; });
+                if (it == row.end()) it = row.emplace(row.end(), cc, 0.0);
+                it->second += a * t[j];
+            }
+            std::sort(row.begin(), row.end());
+            const double w = omega / dF[i];
+            for (const auto& e : row) {
+                const double base = (e.first == agg[i]) ? t[i] : 0.0;
+                oc.push_back(e.first);
+                ov.push_back(base - w * e.second);
+            }
+            P.ptr[i + 1] = (int32_t)(row.size());  // row length; prefix-summed below
         }
-        std::sort(row.begin(), row.end());
-        const double w = omega / dF[i];
-        for (const auto& e : row) {
-            const double base = (e.first == agg[i]) ? t[i] : 0.0;
-            P.col.push_back(e.first);
-            P.val.push_back(base - w * e.second);
-        }
-        P.ptr[i + 1] = (int32_t)P.col.size();
-    }
+    });
+    for (int64_t i = 0; i < n; ++i) P.ptr[i + 1] += P.ptr[i];
+    P.col.resize(P.ptr[n]);
+    P.val.resize(P.ptr[n]);
+    parallel_for(C, [&](int64_t c) {
+        const int64_t lo = n * c / C;
+        std::copy(ccol[c].begin(), ccol[c].end(), P.col.begin() + P.ptr[lo]);
+        std::copy(cval[c].begin(), cval[c].end(), P.val.begin() + P.ptr[lo]);
+    });
 }
 
 // R = P^T (Sec. 2), columns ascending.
@@ -219,15 +259,17 @@ void host_transpose(const HostCsr& P, HostCsr& R) {
 void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const amg_params& prm,
                         std::vector<double>& d) {
     d.resize(A.nrows);
-    for (int64_t i = 0; i < A.nrows; ++i) {
-        if (prm.smoother == AMG_SMOOTHER_SPAI0) {
-            double s2 = 0.0;
-            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s2 += A.val[k] * A.val[k];
-            d[i] = dg[i] / s2;
-        } else {
-            d[i] = prm.jacobi_omega / dg[i];
+    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            if (prm.smoother == AMG_SMOOTHER_SPAI0) {
+                double s2 = 0.0;
+                for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s2 += A.val[k] * A.val[k];
+                d[i] = dg[i] / s2;
+            } else {
+                d[i] = prm.jacobi_omega / dg[i];
+            }
         }
-    }
+    });
 }
 
 // Coarsest direct solver (Algorithm 1, last step): LU with partial pivoting

@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "amg_internal.h"
+#include "host_parallel.h"
 #include "handle.h"
 
 namespace amg {
@@ -157,9 +158,6 @@ static void build_tail(amg_handle* h) {
         plan.nph = (int)ph.size();
         plan.phases = halloc<TailPhase>(h, ph.size());
         AMG_CUDA(cudaMemcpy(plan.phases, ph.data(), ph.size() * sizeof(TailPhase), cudaMemcpyHostToDevice));
-        plan.bar = halloc<unsigned int>(h, 2);
-        AMG_CUDA(cudaMemset(plan.bar, 0, 2 * sizeof(unsigned int)));
-        plan.err = dev_err_ptr();
     }
     h->tail_ls = ls;
 }
@@ -186,7 +184,9 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         AMG_CUDA(cudaMemcpy(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice));
         {   // values scaled by the smoother diagonal, for the fused first pre-sweep
             std::vector<double> vd(A.nnz());
-            for (int64_t k = 0; k < A.nnz(); ++k) vd[k] = A.val[k] * L.dhost[A.col[k]];
+            parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+                for (int64_t k = A.ptr[lo]; k < A.ptr[hi]; ++k) vd[k] = A.val[k] * L.dhost[A.col[k]];
+            });
             L.A.vald = halloc<double>(h, A.nnz() + kPad);
             AMG_CUDA(cudaMemset(L.A.vald, 0, (A.nnz() + kPad) * sizeof(double)));
             AMG_CUDA(cudaMemcpy(L.A.vald, vd.data(), A.nnz() * sizeof(double), cudaMemcpyHostToDevice));

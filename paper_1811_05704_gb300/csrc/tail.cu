@@ -5,10 +5,14 @@
 // again in launch and pipeline-fill latency.  The tail kernel therefore runs
 // Algorithm 2 from level ls down to the coarsest level and back up to ls as a
 // list of phases -- pre-sweep + residual, restriction, dense coarsest solve,
-// prolongation + correction, post-sweep -- in one cooperative launch, with a
-// grid-wide barrier between phases.  The data of these levels is small enough
-// to stay in L2, so rows are read with plain loads by warps (vw lanes per
-// row) rather than streamed.
+// prolongation + correction, post-sweep -- in one launch of a single
+// thread-block cluster (16 CTAs of 1024 threads where the device allows, else
+// 8), with the cluster's hardware barrier between phases: all CTAs of a
+// cluster are resident together, so the barrier needs no spinning on global
+// memory, and its release/acquire semantics at cluster scope make each
+// phase's global-memory results visible to the next.  The data of these
+// levels is small enough to stay in L2, so rows are read with plain loads by
+// warps (vw lanes per row) rather than streamed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,43 +22,19 @@
 
 namespace amg {
 
-// Grid-wide barrier for a cooperative launch: bar[0] counts arrivals, bar[1]
-// is the generation.  The wait is bounded (2 s after arrival); on timeout bit
-// 8 is recorded in *err and the block continues (results are then reported
-// invalid by the host).
-__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int* gen = bar + 1;
-        const unsigned int g = *gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            uint64_t t0;
-            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
-            while (*gen == g) {
-                __nanosleep(64);
-                uint64_t t;
-                asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-                if (t - t0 > 2000000000ull) {
-                    atomicOr(err, 8);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
+constexpr int kTailThreads = 1024;
+
+// Every thread of every CTA of the cluster arrives; the wait returns once all
+// have arrived (hardware barrier, no polling loop).
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n"
+        "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 template <typename VT, typename T>
-__global__ void __launch_bounds__(256)
-k_tail(const TailPhase* __restrict__ phases, int nph, unsigned int* bar, int* err,
-       const int* __restrict__ skip) {
+__global__ void __launch_bounds__(kTailThreads, 1)
+k_tail(const TailPhase* __restrict__ phases, int nph, const int* __restrict__ skip) {
     if (skip && *skip) return;  // the same flag value in every block: uniform
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -104,33 +84,52 @@ k_tail(const TailPhase* __restrict__ phases, int nph, unsigned int* bar, int* er
                 }
             }
         }
-        if (p + 1 < nph) grid_barrier(bar, err);
+        if (p + 1 < nph) cluster_barrier();
     }
+}
+
+// Cluster size: 16 CTAs where the device can place such a cluster of this
+// kernel, else 8 (the portable size).
+template <typename VT, typename T>
+static int tail_cluster_size() {
+    static const int size = [] {
+        AMG_CUDA(cudaFuncSetAttribute(k_tail<VT, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kTailThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_tail<VT, T>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+        return clusters > 0 ? 16 : 8;
+    }();
+    return size;
 }
 
 template <typename VT, typename T>
 static void launch_tail_t(const TailPlan& plan, const int* skip, cudaStream_t s) {
-    // once per template instance (thread-safe static initialisation)
-    static const int2 occ = [] {
-        int dev = 0, sm_count = 0, blocks = 0;
-        AMG_CUDA(cudaGetDevice(&dev));
-        AMG_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
-        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_tail<VT, T>, 256, 0));
-        return make_int2(std::max(1, std::min(blocks, 4)), sm_count);
-    }();
-    const int per_sm = occ.x, sms = occ.y;
+    const int c = tail_cluster_size<VT, T>();
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(per_sm * sms);
-    cfg.blockDim = dim3(256);
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kTailThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_tail<VT, T>, (const TailPhase*)plan.phases, plan.nph, plan.bar,
-                                plan.err, skip));
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_tail<VT, T>, (const TailPhase*)plan.phases, plan.nph, skip));
 }
 
 void launch_tail(const TailPlan& plan, bool f32, const int* skip, cudaStream_t s) {
