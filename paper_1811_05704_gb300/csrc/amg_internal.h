@@ -152,7 +152,8 @@ void launch_residual_plain(const DevCsr& A, const double* f, const double* x, do
 void launch_scale(const double* d, const double* f, double* x, int64_t n, const int* skip,
                   cudaStream_t s);
 int vec_grid(int64_t n);
-int stream_grid(int ntiles);
+int stream_grid(int ntiles, int ctas_per_sm);  // persistent grid of the streaming engine
+constexpr int kStreamCtasMax = 3;             // most resident streaming CTAs per SM (any value type)
 void set_stream_options(bool pdl);
 int read_and_clear_dev_err();
 void enqueue_dev_err_copy(int* host_dst, cudaStream_t s);

@@ -233,7 +233,7 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             std::memset(h->st_in, 0, sizeof(KState));
             std::memset(h->st_out, 0, sizeof(KState));
             h->stride = std::max(std::max<int>(h->lev[0].A.nblk, vec_grid(h->n)),
-                                 stream_grid(std::max(1, h->lev[0].A.ntiles)));
+                                 stream_grid(std::max(1, h->lev[0].A.ntiles), kStreamCtasMax));
             h->dev_bytes += 2 * (int64_t)h->stride * 8 + 512;
             h->partial = dev_alloc<double>(2 * (size_t)h->stride);
             h->dev_allocs.push_back(h->partial);

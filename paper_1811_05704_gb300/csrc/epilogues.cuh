@@ -4,6 +4,9 @@
 //   ndot              number of dot products it contributes (0..2)
 //   nvec, vptr(k), vbytes(k)
 //                     row-indexed input vectors (internal, padded buffers)
+//                     ... and optionally vslot(k), a compile-time bound on
+//                     vbytes(k) that sizes the vector's shared-memory slot
+//                     (8 bytes when absent)
 //                     that the streaming engine copies into shared memory with
 //                     the tile; an epilogue that reads caller memory by row
 //                     (the residual of the initial guess) lists none and
@@ -229,6 +232,7 @@ struct EpiPre32 {  // as EpiPre, with matrix values a_ij d_j in float32
         return k == 0 ? (const void*)d : (f64 ? (const void*)f64 : (const void*)f32);
     }
     __device__ int vbytes(int k) const { return (k == 1 && f64) ? 8 : 4; }
+    __host__ __device__ static constexpr int vslot(int k) { return k == 1 ? 8 : 4; }
     __device__ float xg(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
     __device__ Pre load(int r, const VecTile& v) const {
         return {v.at<float>(0, r), f64 ? (float)v.at<double>(1, r) : v.at<float>(1, r)};
@@ -258,6 +262,7 @@ struct EpiSmooth32 {
                       : (const void*)w;
     }
     __device__ int vbytes(int k) const { return (k == 3 || (k == 2 && f64)) ? 8 : 4; }
+    __host__ __device__ static constexpr int vslot(int k) { return k < 2 ? 4 : 8; }
     __device__ float xg(int c) const { return __ldg(x + c); }
     __device__ Pre load(int r, const VecTile& v) const {
         return {v.at<float>(0, r), v.at<float>(1, r),
@@ -279,6 +284,7 @@ struct EpiProlong32 {
     float* __restrict__ x;
     __device__ const void* vptr(int) const { return x; }
     __device__ int vbytes(int) const { return 4; }
+    __host__ __device__ static constexpr int vslot(int) { return 4; }
     __device__ float xg(int c) const { return __ldg(xc + c); }
     __device__ Pre load(int r, const VecTile& v) const { return {v.at<float>(0, r)}; }
     __device__ void store(int r, float s, const Pre& p, double&, double&) const { x[r] = p.x + s; }

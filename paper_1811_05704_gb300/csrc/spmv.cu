@@ -21,6 +21,7 @@
 #include <atomic>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "amg_internal.h"
 #include "device_common.cuh"
@@ -42,7 +43,13 @@ namespace amg {
 // the solve overlap their pipeline fill with the predecessor's tail.
 constexpr int kCons = kConsumers;
 constexpr int kStages = 3;
-constexpr int kCtasPerSm = 2;
+
+// Resident CTAs per SM: the shared-memory ring of a float64 kernel
+// (3 stages of about 26 KB) allows two, that of a float32 or bfloat16 kernel
+// (about 24 KB or less per stage) three.  More tiles in flight per SM hide
+// more of the gather latency.
+template <typename VT>
+__host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 2 : kStreamCtasMax; }
 
 __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 
@@ -52,19 +59,39 @@ __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 template <typename VT>
 __host__ __device__ constexpr int nz_align() { return sizeof(VT) >= 4 ? 4 : 16 / (int)sizeof(VT); }
 
-template <typename VT, int RMAX, int NV>
+// Bytes per element of an epilogue's row-indexed vector k in shared memory:
+// the epilogue's vslot(k) if it declares one (it must be at least vbytes(k)
+// for every instance), else 8.
+template <typename Epi, typename = void>
+struct VecSlots {
+    __host__ __device__ static constexpr int at(int) { return 8; }
+};
+template <typename Epi>
+struct VecSlots<Epi, std::void_t<decltype(Epi::vslot(0))>> {
+    __host__ __device__ static constexpr int at(int k) { return Epi::vslot(k); }
+};
+
+template <typename VT, int RMAX, typename Epi>
 struct StreamLayout {
+    static constexpr int NV = Epi::nvec;
     static constexpr int rp_n = RMAX + 8;       // row pointers of the tile (+ alignment slack)
     static constexpr int nz_n = kTileNnz + 2 * nz_align<VT>();  // nonzeros of the tile (+ alignment slack)
-    static constexpr int vec_n = RMAX + 8;      // row-indexed vector slice, 8-byte slots
+    static constexpr int vec_n = RMAX + 8;      // rows of a row-indexed vector slice (+ alignment slack)
     static constexpr size_t rp_bytes = (size_t)rp_n * 4;
     static constexpr size_t col_bytes = (size_t)nz_n * 4;
     static constexpr size_t val_bytes = (size_t)nz_n * sizeof(VT);
-    static constexpr size_t vec_bytes = (size_t)vec_n * 8;
-    static constexpr size_t stage = rp_bytes + col_bytes + val_bytes + NV * vec_bytes;
+    __host__ __device__ static constexpr size_t vec_bytes(int k) {
+        return ((size_t)vec_n * VecSlots<Epi>::at(k) + 15) / 16 * 16;
+    }
+    __host__ __device__ static constexpr size_t vec_off(int k) {
+        size_t o = 0;
+        for (int j = 0; j < k; ++j) o += vec_bytes(j);
+        return o;
+    }
+    static constexpr size_t stage = rp_bytes + col_bytes + val_bytes + vec_off(NV);
     static constexpr size_t header = 128;
     static constexpr size_t total = header + kStages * stage;
-    static_assert(rp_bytes % 16 == 0 && col_bytes % 16 == 0 && val_bytes % 16 == 0 && vec_bytes % 16 == 0,
+    static_assert(rp_bytes % 16 == 0 && col_bytes % 16 == 0 && val_bytes % 16 == 0 && stage % 16 == 0,
                   "bulk-copy destinations must stay 16-byte aligned");
 };
 
@@ -125,13 +152,13 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename VT, typename Epi, int RMAX>
-__global__ void __launch_bounds__(kCons + 32, kCtasPerSm)
+__global__ void __launch_bounds__(kCons + 32, stream_ctas<VT>())
 k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
          const VT* __restrict__ val, const int2* __restrict__ tiles, int ntiles, int vw, Epi epi,
          Reduce red, const int* __restrict__ skip) {
     using acc_t = typename Epi::acc_t;
     constexpr int NV = Epi::nvec;
-    using L = StreamLayout<VT, RMAX, NV>;
+    using L = StreamLayout<VT, RMAX, Epi>;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* empty = full + kStages;
@@ -141,7 +168,7 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     auto col_of = [&](int s) { return reinterpret_cast<int*>(stage_of(s) + L::rp_bytes); };
     auto val_of = [&](int s) { return reinterpret_cast<VT*>(stage_of(s) + L::rp_bytes + L::col_bytes); };
     auto vec_of = [&](int s, int k) {
-        return stage_of(s) + L::rp_bytes + L::col_bytes + L::val_bytes + k * L::vec_bytes;
+        return stage_of(s) + L::rp_bytes + L::col_bytes + L::val_bytes + L::vec_off(k);
     };
 
     const int tid = threadIdx.x;
@@ -360,7 +387,7 @@ static thread_local bool g_pdl = true;
 
 void set_stream_options(bool pdl) { g_pdl = pdl; }
 
-int stream_grid(int ntiles) {
+int stream_grid(int ntiles, int ctas_per_sm) {
     int sms = g_sm_count.load();
     if (sms == 0) {
         int dev = 0;
@@ -368,7 +395,7 @@ int stream_grid(int ntiles) {
         AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         g_sm_count.store(sms);
     }
-    return std::max(1, std::min(ntiles, kCtasPerSm * sms));
+    return std::max(1, std::min(ntiles, ctas_per_sm * sms));
 }
 
 int* dev_err_ptr() {
@@ -391,15 +418,26 @@ int read_and_clear_dev_err() {
 template <typename VT, typename Epi, int RMAX>
 static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
                           const int* skip, cudaStream_t s) {
-    const int grid = stream_grid(A.ntiles);
-    if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
-    const size_t smem = StreamLayout<VT, RMAX, Epi::nvec>::total;
-    static std::atomic<bool> configured{false};  // once per template instance
-    if (!configured.load()) {
+    const size_t smem = StreamLayout<VT, RMAX, Epi>::total;
+    // once per template instance (thread-safe static initialisation): the
+    // shared-memory limit, and the CTAs per SM the grid is sized for -- the
+    // resident count the device reports, at most stream_ctas<VT>(), so that
+    // the persistent grid is one wave.  Kernels that can hold more than two
+    // CTAs per SM ask for the largest shared-memory carveout; the float64
+    // kernels keep the default, whose larger L1 serves their gathers.
+    static const int ctas = [smem] {
         AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        configured.store(true);
-    }
+        if (stream_ctas<VT>() > 2)
+            AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>,
+                                          cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0;
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream<VT, Epi, RMAX>, kCons + 32,
+                                                               smem));
+        return std::max(1, std::min(per_sm, stream_ctas<VT>()));
+    }();
+    const int grid = stream_grid(A.ntiles, ctas);
+    if (Epi::ndot > 0 && grid > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kCons + 32);
