@@ -73,6 +73,23 @@ def kernel_bytes(info):
     }
 
 
+def kernel_bytes_mixed(info, vb):
+    """As kernel_bytes for the float32 V-cycle with vb-byte matrix values (4:
+    float32, 2: bfloat16): float32 level vectors, except the finest level's
+    float64 residual input and correction output."""
+    n0, z0 = info["rows"][0], info["nnz"][0]
+    n1 = info["rows"][1] if info["levels"] > 1 else 0
+    zp = info["nnz_p"][0]
+    e = vb + 4
+    return {
+        "spmv_dot": 12 * z0 + 4 * n0 + 8 * n0 + 8 * n0,       # FP64, as kernel_bytes
+        "presmooth_l0": e * z0 + 4 * n0 + 12 * n0 + 8 * n0,   # A, d (f32) r (f64) read, x t (f32) written
+        "restrict_l0": e * zp + 4 * n1 + 4 * n0 + 4 * n1,     # R, t, f_1
+        "prolong_l0": e * zp + 4 * n0 + 4 * n1 + 8 * n0,      # P, x_1, x read+write
+        "postsmooth_l0": e * z0 + 4 * n0 + 4 * n0 + 12 * n0 + 8 * n0,  # A, x, d r, z (f64)
+    }
+
+
 # GB300's FP64 vector rate: 1.25 TFLOP/s nominal, i.e. about 4 FP64 flops (two
 # fused multiply-adds) per clock per SM at 152 SMs x 2.07 GHz.  The FP64 CSR
 # kernels do 2 flops per 12 bytes, so at 6.7 TB/s they need 1.1 TFLOP/s: they
@@ -541,9 +558,22 @@ def main():
             torch.cuda.synchronize()
             t32 = e0.elapsed_time(e1) / 1e3 / reps
             err = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+            # per-kernel event times of an instrumented solve of this form
+            x.zero_()
+            _, _, _, pms, pln = amg.amg_solve_profile(S32.handle, ft, x, RTOL, MAXITER)
+            kbm = kernel_bytes_mixed(info, 4 if name == "fp32" else 2)
+            mk = {k: {"launches": pln[k], "ms": round(pms[k], 4),
+                      "gbs": (round(kbm[k] * pln[k] / (pms[k] / 1e3) / 1e9, 1) if k in kbm and pms[k] > 0 else None)}
+                  for k in pms}
+            mdom = max(kbm, key=lambda k: pms[k])
+            mavg = pms[mdom] / max(1, pln[mdom])
+            mach = kbm[mdom] / (mavg / 1e3) / 1e9
             mixed[name] = {"value": 1.0 / t32, "unit": "solves/s", "solve_s": t32, "iterations": it32,
                            "relres": rr32, "status": st32, "precision": desc, "rel_diff_vs_fp64_x": err,
-                           "speedup_vs_fp64": solve_s / t32}
+                           "speedup_vs_fp64": solve_s / t32, "kernels": mk,
+                           "roofline": {"bound": "hbm", "kernel": mdom, "achieved": mach, "peak": peak,
+                                        "unit": "GB/s", "frac": mach / peak,
+                                        "algorithmic_bytes_per_launch": kbm[mdom], "avg_launch_ms": mavg}}
             S32.close()
 
     batched = None

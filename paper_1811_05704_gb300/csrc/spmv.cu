@@ -259,12 +259,20 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                     const int row = inf.x + rb + grp;
                     const bool active = rb + grp < nrows;
                     typename Epi::Pre pre{};
-                    if (active && lane == 0) pre = epi.load(row, vt);
                     acc_t sum = acc_t(0);
+                    if (active && lane == 0) {
+                        pre = epi.load(row, vt);
+                        if constexpr (Seeding<Epi>::sign != 0) sum = epi.seed(pre);
+                    }
                     if (active) {
                         const int kb = rp[row - inf.z] - inf.w, ke = rp[row + 1 - inf.z] - inf.w;
+                        if constexpr (Seeding<Epi>::sign < 0) {
 #pragma unroll 4
-                        for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
+                            for (int k = kb + lane; k < ke; k += vw) sum -= (acc_t)vs[k] * epi.xg(cs[k]);
+                        } else {
+#pragma unroll 4
+                            for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
+                        }
                     }
                     for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
                     if (active && lane == 0) {
@@ -376,7 +384,12 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     if (warp_rows) acc = (tid < nr) ? rowsum[tid] : acc_t(0);
 
     double d0 = 0.0, d1 = 0.0;
-    if (tid < nr) epi.store(r0 + tid, acc, pre, d0, d1);
+    if (tid < nr) {
+        // this engine sums the row first; a seeded epilogue gets seed -/+ sum
+        if constexpr (Seeding<Epi>::sign < 0) acc = epi.seed(pre) - acc;
+        if constexpr (Seeding<Epi>::sign > 0) acc = epi.seed(pre) + acc;
+        epi.store(r0 + tid, acc, pre, d0, d1);
+    }
     if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
 }
 
