@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "amg_internal.h"
 
@@ -390,15 +391,45 @@ k_num_wide(int32_t nwide, const int32_t* __restrict__ rows, const int32_t* __res
 
 }  // namespace
 
+// Device temporaries of one product, freed when it goes out of scope (also
+// when an error is thrown); the output arrays are freed too unless kept.
+struct SpgemmScratch {
+    std::vector<void*> tmp;
+    DevCsr* out = nullptr;
+    bool keep = false;
+    template <typename T>
+    T* get(size_t n) {
+        T* p = dev_alloc<T>(n);
+        tmp.push_back(p);
+        return p;
+    }
+    ~SpgemmScratch() {
+        for (void* p : tmp) dev_free(p);
+        if (out && !keep) {
+            dev_free(out->ptr);
+            dev_free(out->col);
+            dev_free(out->val);
+            out->ptr = nullptr;
+            out->col = nullptr;
+            out->val = nullptr;
+        }
+    }
+};
+
 void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) {
     const int32_t m = A.nrows;
     C.nrows = m;
     C.ncols = B.ncols;
-    int32_t* count = dev_alloc<int32_t>(m > 0 ? m : 1);
-    int32_t* big = dev_alloc<int32_t>(m > 0 ? m : 1);
-    int32_t* nbig = dev_alloc<int32_t>(2);  // [0]: rows for the block kernels, [1]: wide rows
-    int32_t* wide = dev_alloc<int32_t>(m > 0 ? m : 1);
-    int* err = dev_alloc<int>(1);
+    C.ptr = nullptr;
+    C.col = nullptr;
+    C.val = nullptr;
+    SpgemmScratch S;
+    S.out = &C;
+    int32_t* count = S.get<int32_t>(m > 0 ? m : 1);
+    int32_t* big = S.get<int32_t>(m > 0 ? m : 1);
+    int32_t* nbig = S.get<int32_t>(2);  // [0]: rows for the block kernels, [1]: wide rows
+    int32_t* wide = S.get<int32_t>(m > 0 ? m : 1);
+    int* err = S.get<int>(1);
     AMG_CUDA(cudaMemsetAsync(nbig, 0, 2 * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     C.ptr = dev_alloc<int32_t>(m + 1 + kPad);
@@ -439,13 +470,11 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
         const int64_t per_block = (int64_t)C.ncols * 8 + words * 4;
         const int64_t cap = std::max<int64_t>(1, (int64_t(1) << 30) / per_block);  // <= 1 GiB of scratch
         wgrid_wide = (int)std::min<int64_t>(std::min<int64_t>(hwide, 2 * (int64_t)sms), cap);
-        unsigned* mark = dev_alloc<unsigned>((size_t)(wgrid_wide * words));
+        unsigned* mark = S.get<unsigned>((size_t)(wgrid_wide * words));
         AMG_CUDA(cudaMemsetAsync(mark, 0, (size_t)(wgrid_wide * words) * sizeof(unsigned), s));
         k_sym_wide<<<wgrid_wide, kBlockThreads, 0, s>>>(hwide, wide, A.ptr, A.col, B.ptr, B.col, mark, words,
                                                         count);
         AMG_CUDA(cudaGetLastError());
-        AMG_CUDA(cudaStreamSynchronize(s));
-        dev_free(mark);
     }
     k_scan<<<1, 1024, 0, s>>>(m, count, C.ptr, err);
     AMG_CUDA(cudaGetLastError());
@@ -454,11 +483,7 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     AMG_CUDA(cudaMemcpyAsync(&nnz, C.ptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaStreamSynchronize(s));
-    auto cleanup = [&]() { dev_free(count); dev_free(big); dev_free(nbig); dev_free(wide); dev_free(err); };
     if (herr) {
-        cleanup();
-        dev_free(C.ptr);
-        C.ptr = nullptr;
         if (herr & 4) fail(AMG_ERR_TOO_LARGE, "Galerkin product has more than 2^31 nonzeros");
         fail(AMG_ERR_CUDA, "sparse product symbolic phase: hash table overflow");
     }
@@ -481,11 +506,9 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
                                                                 B.col, B.val, C.ptr, C.col, C.val, err);
         AMG_CUDA(cudaGetLastError());
     }
-    double* acc = nullptr;
-    unsigned* mark = nullptr;
     if (hwide > 0) {
-        acc = dev_alloc<double>((size_t)wgrid_wide * C.ncols);
-        mark = dev_alloc<unsigned>((size_t)(wgrid_wide * words));
+        double* acc = S.get<double>((size_t)wgrid_wide * C.ncols);
+        unsigned* mark = S.get<unsigned>((size_t)(wgrid_wide * words));
         AMG_CUDA(cudaMemsetAsync(acc, 0, (size_t)wgrid_wide * C.ncols * sizeof(double), s));
         AMG_CUDA(cudaMemsetAsync(mark, 0, (size_t)(wgrid_wide * words) * sizeof(unsigned), s));
         k_num_wide<<<wgrid_wide, kBlockThreads, 0, s>>>(hwide, wide, A.ptr, A.col, A.val, B.ptr, B.col, B.val,
@@ -495,10 +518,8 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     }
     AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaStreamSynchronize(s));
-    cleanup();
-    if (acc) dev_free(acc);
-    if (mark) dev_free(mark);
     if (herr) fail(AMG_ERR_CUDA, "sparse product numeric phase inconsistent with its symbolic phase");
+    S.keep = true;
 }
 
 }  // namespace amg
