@@ -255,6 +255,60 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                 for (int k = 0; k < 4; ++k) vt.base[k] = (k < NV) ? vec_of(s, k) : nullptr;
                 vt.row0 = inf.z;
                 const int nrows = inf.y - inf.x;
+                if (nrows > ngroups) {
+                    // two consumer passes in this tile (short rows): take the
+                    // rows of both passes together, so that each lane has the
+                    // gathers of two rows in flight at once
+                    for (int rb = 0; rb < nrows; rb += 2 * ngroups) {  // same trip count in every lane
+                        const int rowA = inf.x + rb + grp, rowB = rowA + ngroups;
+                        const bool actA = rb + grp < nrows, actB = rb + ngroups + grp < nrows;
+                        typename Epi::Pre preA{}, preB{};
+                        acc_t sumA = acc_t(0), sumB = acc_t(0);
+                        if (lane == 0) {
+                            if (actA) preA = epi.load(rowA, vt);
+                            if (actB) preB = epi.load(rowB, vt);
+                            if constexpr (Seeding<Epi>::sign != 0) {
+                                if (actA) sumA = epi.seed(preA);
+                                if (actB) sumB = epi.seed(preB);
+                            }
+                        }
+                        int kA = 0, keA = 0, kB = 0, keB = 0;
+                        if (actA) { kA = rp[rowA - inf.z] - inf.w + lane; keA = rp[rowA + 1 - inf.z] - inf.w; }
+                        if (actB) { kB = rp[rowB - inf.z] - inf.w + lane; keB = rp[rowB + 1 - inf.z] - inf.w; }
+#pragma unroll 2
+                        for (;;) {
+                            const bool a = kA < keA, b = kB < keB;
+                            if (!a && !b) break;
+                            if constexpr (Seeding<Epi>::sign < 0) {
+                                if (a) sumA -= (acc_t)vs[kA] * epi.xg(cs[kA]);
+                                if (b) sumB -= (acc_t)vs[kB] * epi.xg(cs[kB]);
+                            } else {
+                                if (a) sumA += (acc_t)vs[kA] * epi.xg(cs[kA]);
+                                if (b) sumB += (acc_t)vs[kB] * epi.xg(cs[kB]);
+                            }
+                            kA += vw;
+                            kB += vw;
+                        }
+                        for (int o = vw >> 1; o > 0; o >>= 1) {
+                            sumA += __shfl_xor_sync(0xffffffffu, sumA, o, vw);
+                            sumB += __shfl_xor_sync(0xffffffffu, sumB, o, vw);
+                        }
+                        if (lane == 0) {
+                            double e0 = 0.0, e1 = 0.0;
+                            if (actA) {
+                                epi.store(rowA, sumA, preA, e0, e1);
+                                d0 += e0;
+                                d1 += e1;
+                            }
+                            if (actB) {
+                                e0 = e1 = 0.0;
+                                epi.store(rowB, sumB, preB, e0, e1);
+                                d0 += e0;
+                                d1 += e1;
+                            }
+                        }
+                    }
+                } else
                 for (int rb = 0; rb < nrows; rb += ngroups) {  // same trip count in every lane
                     const int row = inf.x + rb + grp;
                     const bool active = rb + grp < nrows;
