@@ -255,8 +255,10 @@ amg_status amg_spmv_dot_noalloc(const amg_csr *A, const double *x, double *y, do
  * idle, or a new matrix whose estimated device memory fits the HBM budget
  * after evicting idle resident hierarchies, least recently used first.  A new
  * matrix larger than the whole budget runs alone.  Admitted requests run
- * concurrently, so their kernels overlap on the GPU.  Every solve is
- * deterministic, so a request's result does not depend on what else runs.
+ * concurrently, so their kernels overlap on the GPU.  A set-up that runs out
+ * of device memory is retried once after evicting every idle hierarchy.
+ * Every solve is deterministic, so a request's result does not depend on
+ * what else runs.
  * Thread-safe: any thread may submit and wait. */
 typedef struct amg_server amg_server;
 

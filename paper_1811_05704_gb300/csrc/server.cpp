@@ -214,6 +214,23 @@ void worker(amg_server* s) {
             c.val = r->A.val.data();
             c.on_device = 0;
             status = amg_setup(&c, &r->prm, st, &h);
+            if (status == AMG_ERR_OOM) {
+                // the charge underestimated this hierarchy or other memory is
+                // in use: free every idle resident hierarchy and try once more
+                std::vector<amg_handle*> idle;
+                {
+                    std::lock_guard<std::mutex> lk(s->m);
+                    for (auto q = s->resident.begin(); q != s->resident.end();) {
+                        if (q->second.busy) { ++q; continue; }
+                        s->in_use -= q->second.bytes;
+                        idle.push_back(q->second.h);
+                        q = s->resident.erase(q);
+                        s->evictions++;
+                    }
+                }
+                for (amg_handle* e : idle) amg_free(e);
+                if (!idle.empty()) status = amg_setup(&c, &r->prm, st, &h);
+            }
             if (status != AMG_OK) err = amg_last_error();
         } else {
             h->stream = st;  // run on this slot's stream

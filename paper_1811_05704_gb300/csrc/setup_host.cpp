@@ -178,14 +178,16 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
                 if (A.col[k] != i && !s[k]) weak += A.val[k];
             dF[i] = dg[i] - weak;
         }
+        double rmax = 0.0;  // written once per chunk (no false sharing between threads)
         for (int64_t i = lo; i < hi; ++i) {
             double row = 0.0;
             for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
                 if (A.col[k] == i) row += std::fabs(dF[i]);
                 else if (s[k]) row += std::fabs(A.val[k]);
             }
-            rho_c[c] = std::max(rho_c[c], row / std::fabs(dF[i]));
+            rmax = std::max(rmax, row / std::fabs(dF[i]));
         }
+        rho_c[c] = rmax;
     });
     double rho = 0.0;
     for (double r : rho_c) rho = std::max(rho, r);
@@ -199,8 +201,10 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
     P.ptr.assign(n + 1, 0);
     parallel_rows(n, [&](int c, int64_t lo, int64_t hi) {
         std::vector<std::pair<int32_t, double>> row;  // (coarse column, s_ij), few entries
-        std::vector<int32_t>& oc = ccol[c];
-        std::vector<double>& ov = cval[c];
+        // thread-local output, moved into place at the end (the vector
+        // objects of neighbouring chunks share cache lines)
+        std::vector<int32_t> oc;
+        std::vector<double> ov;
         oc.reserve(A.ptr[hi] - A.ptr[lo] + (hi - lo));
         ov.reserve(A.ptr[hi] - A.ptr[lo] + (hi - lo));
         for (int64_t i = lo; i < hi; ++i) {
@@ -225,6 +229,8 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
             }
             P.ptr[i + 1] = (int32_t)(row.size());  // row length; prefix-summed below
         }
+        ccol[c] = std::move(oc);
+        cval[c] = std::move(ov);
     });
     for (int64_t i = 0; i < n; ++i) P.ptr[i + 1] += P.ptr[i];
     P.col.resize(P.ptr[n]);
@@ -236,22 +242,57 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
     });
 }
 
-// R = P^T (Sec. 2), columns ascending.
+// R = P^T (Sec. 2), columns ascending.  A counting sort over chunks of rows
+// of P: each chunk counts its entries per column, the counts are laid out
+// column by column in chunk order, and each chunk scatters its entries, so
+// the entries of a column stay in row order (the result is the serial
+// transpose's).
 void host_transpose(const HostCsr& P, HostCsr& R) {
     R.nrows = P.ncols;
     R.ncols = P.nrows;
     R.ptr.assign(R.nrows + 1, 0);
     R.col.resize(P.nnz());
     R.val.resize(P.nnz());
-    for (int64_t k = 0; k < P.nnz(); ++k) R.ptr[P.col[k] + 1]++;
-    for (int64_t c = 0; c < R.nrows; ++c) R.ptr[c + 1] += R.ptr[c];
-    std::vector<int32_t> pos(R.ptr.begin(), R.ptr.end() - 1);
-    for (int64_t i = 0; i < P.nrows; ++i)
-        for (int32_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
-            const int32_t dst = pos[P.col[k]]++;
-            R.col[dst] = (int32_t)i;
-            R.val[dst] = P.val[k];
+    const int64_t nc = R.nrows, n = P.nrows;
+    // one chunk of rows per thread (at most 16), none for small matrices
+    const int C = row_chunks(n) == 1 ? 1 : (int)host_threads();
+    if (C == 1) {
+        for (int64_t k = 0; k < P.nnz(); ++k) R.ptr[P.col[k] + 1]++;
+        for (int64_t c = 0; c < nc; ++c) R.ptr[c + 1] += R.ptr[c];
+        std::vector<int32_t> pos(R.ptr.begin(), R.ptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+                const int32_t dst = pos[P.col[k]]++;
+                R.col[dst] = (int32_t)i;
+                R.val[dst] = P.val[k];
+            }
+        return;
+    }
+    // cnt[c][j]: entries of chunk c in column j, then their first slot
+    std::vector<std::vector<int32_t>> cnt(C);
+    parallel_for(C, [&](int64_t c) {
+        cnt[c].assign(nc, 0);
+        int32_t* my = cnt[c].data();
+        for (int32_t k = P.ptr[n * c / C]; k < P.ptr[n * (c + 1) / C]; ++k) my[P.col[k]]++;
+    });
+    for (int64_t j = 0; j < nc; ++j) {
+        int32_t at = R.ptr[j];
+        for (int c = 0; c < C; ++c) {
+            const int32_t k = cnt[c][j];
+            cnt[c][j] = at;
+            at += k;
         }
+        R.ptr[j + 1] = at;
+    }
+    parallel_for(C, [&](int64_t c) {
+        int32_t* pos = cnt[c].data();
+        for (int64_t i = n * c / C; i < n * (c + 1) / C; ++i)
+            for (int32_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+                const int32_t dst = pos[P.col[k]]++;
+                R.col[dst] = (int32_t)i;
+                R.val[dst] = P.val[k];
+            }
+    });
 }
 
 // Smoother diagonal (Sec. 3, relaxation): damped Jacobi omega / a_ii, or
