@@ -233,11 +233,22 @@ int* dev_err_ptr();
 
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.
+// C's arrays are stream-ordered allocations on s (free with dev_free_async).
 void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s);
 
 // device memory helpers
 template <typename T>
 T* dev_alloc(size_t count);
 void dev_free(void* p);
+// Stream-ordered device memory (the device's default memory pool): freeing
+// does not synchronise the device, so set-ups and frees on one stream do not
+// stall solves running on other streams.  Memory from dev_alloc_async is
+// freed with dev_free_async.
+void* dev_alloc_async_bytes(size_t bytes, cudaStream_t s);
+template <typename T>
+T* dev_alloc_async(size_t count, cudaStream_t s) {
+    return static_cast<T*>(dev_alloc_async_bytes(count * sizeof(T), s));
+}
+void dev_free_async(void* p, cudaStream_t s);
 
 }  // namespace amg

@@ -118,6 +118,16 @@ void free_tmp(DevCsr& D) {
     D.val = nullptr;
 }
 
+// the outputs of device_spgemm (stream-ordered allocations)
+void free_product(DevCsr& D, cudaStream_t s) {
+    dev_free_async(D.ptr, s);
+    dev_free_async(D.col, s);
+    dev_free_async(D.val, s);
+    D.ptr = nullptr;
+    D.col = nullptr;
+    D.val = nullptr;
+}
+
 // Galerkin products of level l for the systems in `act` (one GPU product
 // pair for all of them); appends A_{l+1} to each.
 void galerkin_batch(std::vector<HSys>& sys, const std::vector<int>& act, int l, cudaStream_t s) {
@@ -141,16 +151,17 @@ void galerkin_batch(std::vector<HSys>& sys, const std::vector<int>& act, int l, 
         device_spgemm(dA, dP, AP, s);
         device_spgemm(dR, AP, Ac, s);
     } catch (...) {
-        free_tmp(dA); free_tmp(dP); free_tmp(dR); free_tmp(AP); free_tmp(Ac);
+        free_tmp(dA); free_tmp(dP); free_tmp(dR); free_product(AP, s); free_product(Ac, s);
         throw;
     }
-    free_tmp(dA); free_tmp(dP); free_tmp(dR); free_tmp(AP);
+    free_tmp(dA); free_tmp(dP); free_tmp(dR); free_product(AP, s);
     std::vector<int32_t> ptr(Ac.nrows + 1), col(Ac.nnz);
     std::vector<double> val(Ac.nnz);
     AMG_CUDA(cudaMemcpy(ptr.data(), Ac.ptr, (Ac.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     AMG_CUDA(cudaMemcpy(col.data(), Ac.col, Ac.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
     AMG_CUDA(cudaMemcpy(val.data(), Ac.val, Ac.nnz * sizeof(double), cudaMemcpyDeviceToHost));
-    free_tmp(Ac);
+    free_product(Ac, s);
+    AMG_CUDA(cudaStreamSynchronize(s));
     for (size_t q = 0; q < act.size(); ++q) {  // split the block diagonal
         const int64_t r0 = coff[q], rn = sys[act[q]].P[l].ncols;
         HostCsr C;

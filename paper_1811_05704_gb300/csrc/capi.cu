@@ -56,6 +56,21 @@ void dev_free(void* p) {
     if (p) cudaFree(p);
 }
 
+void* dev_alloc_async_bytes(size_t bytes, cudaStream_t s) {
+    void* p = nullptr;
+    const cudaError_t e = cudaMallocAsync(&p, bytes > 0 ? bytes : 1, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA,
+             "cudaMallocAsync of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free_async(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 void build_hierarchy(amg_handle* h, HostCsr A);
 amg_status spmv_dot_noalloc(const amg_csr* A, const double* x, double* y, double* dot, void* stream);
 void build_batch(amg_batch* b, const amg_csr* systems);
@@ -111,9 +126,10 @@ static amg_status guarded(F&& body) {
 static void free_handle(amg_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
-    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
-    for (void* p : h->dev_allocs) cudaFree(p);
+    for (void* p : h->dev_allocs) cudaFreeAsync(p, h->stream);  // no device-wide synchronisation
+    cudaStreamSynchronize(h->stream);
     if (h->st_in) cudaFreeHost(h->st_in);
     if (h->st_out) cudaFreeHost(h->st_out);
     if (h->err_host) cudaFreeHost(h->err_host);
@@ -215,17 +231,17 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             AMG_CUDA(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
             build_hierarchy(h, std::move(H));
             auto vec = [&](double*& v) {  // padded: see kPad
-                v = dev_alloc<double>(h->n + kPad);
+                v = dev_alloc_async<double>(h->n + kPad, h->stream);
                 h->dev_allocs.push_back(v);
                 h->dev_bytes += (h->n + kPad) * 8;
-                AMG_CUDA(cudaMemset(v, 0, (h->n + kPad) * sizeof(double)));
+                AMG_CUDA(cudaMemsetAsync(v, 0, (h->n + kPad) * sizeof(double), h->stream));
             };
             for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->rh, &h->v, &h->ph, &h->sv, &h->sh,
                                &h->tv, &h->fbuf, &h->xbuf})
                 vec(*v);
-            h->st = dev_alloc<KState>(1);
+            h->st = dev_alloc_async<KState>(1, h->stream);
             h->dev_allocs.push_back(h->st);
-            AMG_CUDA(cudaMemset(h->st, 0, sizeof(KState)));
+            AMG_CUDA(cudaMemsetAsync(h->st, 0, sizeof(KState), h->stream));
             AMG_CUDA(cudaMallocHost(&h->st_in, sizeof(KState)));
             AMG_CUDA(cudaMallocHost(&h->st_out, sizeof(KState)));
             AMG_CUDA(cudaMallocHost(&h->err_host, sizeof(int)));
@@ -235,11 +251,11 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             h->stride = std::max(std::max<int>(h->lev[0].A.nblk, vec_grid(h->n)),
                                  stream_grid(std::max(1, h->lev[0].A.ntiles), kStreamCtasMax));
             h->dev_bytes += 2 * (int64_t)h->stride * 8 + 512;
-            h->partial = dev_alloc<double>(2 * (size_t)h->stride);
+            h->partial = dev_alloc_async<double>(2 * (size_t)h->stride, h->stream);
             h->dev_allocs.push_back(h->partial);
-            h->counter = dev_alloc<unsigned int>(1);
+            h->counter = dev_alloc_async<unsigned int>(1, h->stream);
             h->dev_allocs.push_back(h->counter);
-            AMG_CUDA(cudaMemset(h->counter, 0, sizeof(unsigned int)));
+            AMG_CUDA(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream));
             // the set-up's own work only: other streams may be solving meanwhile
             AMG_CUDA(cudaStreamSynchronize(h->stream));
             AMG_CUDA(cudaStreamSynchronize(nullptr));

@@ -18,7 +18,7 @@ namespace amg {
 // ------------------------------------------------------------ memory
 template <typename T>
 static T* halloc(amg_handle* h, size_t count) {
-    T* p = dev_alloc<T>(count > 0 ? count : 1);
+    T* p = dev_alloc_async<T>(count > 0 ? count : 1, h->stream);
     h->dev_allocs.push_back(p);
     h->dev_bytes += (int64_t)(count > 0 ? count : 1) * (int64_t)sizeof(T);
     return p;
@@ -35,7 +35,7 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     const std::vector<int32_t> blk = host_row_blocks(ptr, kRowsPerBlock, kTileNnz);
     D.nblk = (int32_t)blk.size() - 1;
     D.blk = halloc<int32_t>(h, blk.size());
-    AMG_CUDA(cudaMemcpy(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    AMG_CUDA(cudaMemcpyAsync(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     int vw = 1, rows_cap = kRowsPerBlock;
     const std::vector<int32_t> tiles = host_tiles(ptr, kTileNnz, rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
@@ -45,7 +45,7 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
         D.vw = vw;
         D.rows_cap = rows_cap;
         int32_t* t = halloc<int32_t>(h, tiles.size());
-        AMG_CUDA(cudaMemcpy(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        AMG_CUDA(cudaMemcpyAsync(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
         D.tiles = reinterpret_cast<int2*>(t);
     }
 }
@@ -53,12 +53,12 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
 static void make_f32(amg_handle* h, DevCsr& D) {
     if (h->prm.precision == AMG_PRECISION_BF16) {
         D.val16 = halloc<uint16_t>(h, D.nnz + kPad);
-        AMG_CUDA(cudaMemset(D.val16, 0, (D.nnz + kPad) * sizeof(uint16_t)));
+        AMG_CUDA(cudaMemsetAsync(D.val16, 0, (D.nnz + kPad) * sizeof(uint16_t), h->stream));
         launch_copy_to_bf16(D.val, D.val16, D.nnz, h->stream);
         return;
     }
     D.val32 = halloc<float>(h, D.nnz + kPad);
-    AMG_CUDA(cudaMemset(D.val32, 0, (D.nnz + kPad) * sizeof(float)));
+    AMG_CUDA(cudaMemsetAsync(D.val32, 0, (D.nnz + kPad) * sizeof(float), h->stream));
     launch_copy_to_f32(D.val, D.val32, D.nnz, h->stream);
 }
 
@@ -69,24 +69,25 @@ static void upload(amg_handle* h, const HostCsr& H, DevCsr& D, int rows_cap_max)
     D.ptr = halloc<int32_t>(h, H.nrows + 1 + kPad);
     D.col = halloc<int32_t>(h, D.nnz + kPad);
     D.val = halloc<double>(h, D.nnz + kPad);
-    AMG_CUDA(cudaMemset(D.ptr, 0, (H.nrows + 1 + kPad) * sizeof(int32_t)));
-    AMG_CUDA(cudaMemset(D.col, 0, (D.nnz + kPad) * sizeof(int32_t)));
-    AMG_CUDA(cudaMemset(D.val, 0, (D.nnz + kPad) * sizeof(double)));
-    AMG_CUDA(cudaMemcpy(D.ptr, H.ptr.data(), (H.nrows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-    AMG_CUDA(cudaMemcpy(D.col, H.col.data(), D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
-    AMG_CUDA(cudaMemcpy(D.val, H.val.data(), D.nnz * sizeof(double), cudaMemcpyHostToDevice));
+    AMG_CUDA(cudaMemsetAsync(D.ptr, 0, (H.nrows + 1 + kPad) * sizeof(int32_t), h->stream));
+    AMG_CUDA(cudaMemsetAsync(D.col, 0, (D.nnz + kPad) * sizeof(int32_t), h->stream));
+    AMG_CUDA(cudaMemsetAsync(D.val, 0, (D.nnz + kPad) * sizeof(double), h->stream));
+    AMG_CUDA(cudaMemcpyAsync(D.ptr, H.ptr.data(), (H.nrows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    AMG_CUDA(cudaMemcpyAsync(D.col, H.col.data(), D.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    AMG_CUDA(cudaMemcpyAsync(D.val, H.val.data(), D.nnz * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     schedule(h, H.ptr, D, rows_cap_max);
 }
 
-static void download(const DevCsr& D, HostCsr& H) {
+static void download(const DevCsr& D, HostCsr& H, cudaStream_t s) {
     H.nrows = D.nrows;
     H.ncols = D.ncols;
     H.ptr.resize(D.nrows + 1);
     H.col.resize(D.nnz);
     H.val.resize(D.nnz);
-    AMG_CUDA(cudaMemcpy(H.ptr.data(), D.ptr, (D.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    AMG_CUDA(cudaMemcpy(H.col.data(), D.col, D.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    AMG_CUDA(cudaMemcpy(H.val.data(), D.val, D.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    AMG_CUDA(cudaMemcpyAsync(H.ptr.data(), D.ptr, (D.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaMemcpyAsync(H.col.data(), D.col, D.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaMemcpyAsync(H.val.data(), D.val, D.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
 }
 
 // Lanes per row for the tail kernel's plain-load rows: about a quarter of the
@@ -157,7 +158,7 @@ static void build_tail(amg_handle* h) {
         TailPlan& plan = p32 ? h->tail32 : h->tail64;
         plan.nph = (int)ph.size();
         plan.phases = halloc<TailPhase>(h, ph.size());
-        AMG_CUDA(cudaMemcpy(plan.phases, ph.data(), ph.size() * sizeof(TailPhase), cudaMemcpyHostToDevice));
+        AMG_CUDA(cudaMemcpyAsync(plan.phases, ph.data(), ph.size() * sizeof(TailPhase), cudaMemcpyHostToDevice, h->stream));
     }
     h->tail_ls = ls;
 }
@@ -180,16 +181,16 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         const std::vector<double> dg = host_diagonal(A);
         host_smoother_diag(A, dg, prm, L.dhost);
         L.d = halloc<double>(h, n + kPad);
-        AMG_CUDA(cudaMemset(L.d, 0, (n + kPad) * sizeof(double)));
-        AMG_CUDA(cudaMemcpy(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        AMG_CUDA(cudaMemsetAsync(L.d, 0, (n + kPad) * sizeof(double), h->stream));
+        AMG_CUDA(cudaMemcpyAsync(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         {   // values scaled by the smoother diagonal, for the fused first pre-sweep
             std::vector<double> vd(A.nnz());
             parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
                 for (int64_t k = A.ptr[lo]; k < A.ptr[hi]; ++k) vd[k] = A.val[k] * L.dhost[A.col[k]];
             });
             L.A.vald = halloc<double>(h, A.nnz() + kPad);
-            AMG_CUDA(cudaMemset(L.A.vald, 0, (A.nnz() + kPad) * sizeof(double)));
-            AMG_CUDA(cudaMemcpy(L.A.vald, vd.data(), A.nnz() * sizeof(double), cudaMemcpyHostToDevice));
+            AMG_CUDA(cudaMemsetAsync(L.A.vald, 0, (A.nnz() + kPad) * sizeof(double), h->stream));
+            AMG_CUDA(cudaMemcpyAsync(L.A.vald, vd.data(), A.nnz() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         }
         bool coarsest = n <= prm.coarse_enough || l + 1 >= prm.max_levels || l + 1 >= AMG_MAX_LEVELS;
         if (!coarsest) {
@@ -213,16 +214,21 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
                 upload(h, R, L.R, 2 * kRowsPerBlock);
                 DevCsr AP, Ac;
                 device_spgemm(L.A, L.P, AP, h->stream);
+                auto free_ap = [&]() {
+                    dev_free_async(AP.ptr, h->stream);
+                    dev_free_async(AP.col, h->stream);
+                    dev_free_async(AP.val, h->stream);
+                };
                 try {
                     device_spgemm(L.R, AP, Ac, h->stream);
                 } catch (...) {
-                    dev_free(AP.ptr); dev_free(AP.col); dev_free(AP.val);
+                    free_ap();
                     throw;
                 }
-                dev_free(AP.ptr); dev_free(AP.col); dev_free(AP.val);
+                free_ap();
                 track(h, Ac);
                 HostCsr next;
-                download(Ac, next);
+                download(Ac, next, h->stream);
                 schedule(h, next.ptr, Ac, kRowsPerBlock);
                 if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
                 h->lev.emplace_back();
@@ -234,17 +240,17 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
             make_f32(h, L.A);
             if (prm.precision == AMG_PRECISION_BF16) {
                 L.A.vald16 = halloc<uint16_t>(h, L.A.nnz + kPad);
-                AMG_CUDA(cudaMemset(L.A.vald16, 0, (L.A.nnz + kPad) * sizeof(uint16_t)));
+                AMG_CUDA(cudaMemsetAsync(L.A.vald16, 0, (L.A.nnz + kPad) * sizeof(uint16_t), h->stream));
                 launch_copy_to_bf16(L.A.vald, L.A.vald16, L.A.nnz, h->stream);
             } else {
                 L.A.vald32 = halloc<float>(h, L.A.nnz + kPad);
-                AMG_CUDA(cudaMemset(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float)));
+                AMG_CUDA(cudaMemsetAsync(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float), h->stream));
                 launch_copy_to_f32(L.A.vald, L.A.vald32, L.A.nnz, h->stream);
             }
             L.d32 = halloc<float>(h, n + kPad);
             std::vector<float> d32(L.dhost.begin(), L.dhost.end());
             d32.resize(n + kPad, 0.0f);
-            AMG_CUDA(cudaMemcpy(L.d32, d32.data(), (n + kPad) * sizeof(float), cudaMemcpyHostToDevice));
+            AMG_CUDA(cudaMemcpyAsync(L.d32, d32.data(), (n + kPad) * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         }
         if (coarsest) {
             if (n > prm.max_coarse_dense)
@@ -254,7 +260,7 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
             host_dense_inverse(A, inv);
             h->nc = (int32_t)n;
             h->cinv = halloc<double>(h, inv.size());
-            AMG_CUDA(cudaMemcpy(h->cinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+            AMG_CUDA(cudaMemcpyAsync(h->cinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
             break;
         }
     }
@@ -267,9 +273,9 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         if (nl == 1) break;
         // padded: the streaming kernels copy 16-byte-aligned row slices
         auto v64 = [&]() { double* p = halloc<double>(h, n + kPad);
-                           AMG_CUDA(cudaMemset(p, 0, (n + kPad) * sizeof(double))); return p; };
+                           AMG_CUDA(cudaMemsetAsync(p, 0, (n + kPad) * sizeof(double), h->stream)); return p; };
         auto v32 = [&]() { float* p = halloc<float>(h, n + kPad);
-                           AMG_CUDA(cudaMemset(p, 0, (n + kPad) * sizeof(float))); return p; };
+                           AMG_CUDA(cudaMemsetAsync(p, 0, (n + kPad) * sizeof(float), h->stream)); return p; };
         if (l > 0) L.f = v64();
         L.x = v64();
         if (!last) { L.y = v64(); L.t = v64(); }

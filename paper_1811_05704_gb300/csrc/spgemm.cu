@@ -391,24 +391,26 @@ k_num_wide(int32_t nwide, const int32_t* __restrict__ rows, const int32_t* __res
 
 }  // namespace
 
-// Device temporaries of one product, freed when it goes out of scope (also
-// when an error is thrown); the output arrays are freed too unless kept.
+// Device temporaries of one product, stream-ordered on the product's stream
+// and freed when it goes out of scope (also when an error is thrown); the
+// output arrays are freed too unless kept.
 struct SpgemmScratch {
+    cudaStream_t s = nullptr;
     std::vector<void*> tmp;
     DevCsr* out = nullptr;
     bool keep = false;
     template <typename T>
     T* get(size_t n) {
-        T* p = dev_alloc<T>(n);
+        T* p = dev_alloc_async<T>(n, s);
         tmp.push_back(p);
         return p;
     }
     ~SpgemmScratch() {
-        for (void* p : tmp) dev_free(p);
+        for (void* p : tmp) dev_free_async(p, s);
         if (out && !keep) {
-            dev_free(out->ptr);
-            dev_free(out->col);
-            dev_free(out->val);
+            dev_free_async(out->ptr, s);
+            dev_free_async(out->col, s);
+            dev_free_async(out->val, s);
             out->ptr = nullptr;
             out->col = nullptr;
             out->val = nullptr;
@@ -424,6 +426,7 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     C.col = nullptr;
     C.val = nullptr;
     SpgemmScratch S;
+    S.s = s;
     S.out = &C;
     int32_t* count = S.get<int32_t>(m > 0 ? m : 1);
     int32_t* big = S.get<int32_t>(m > 0 ? m : 1);
@@ -432,7 +435,7 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     int* err = S.get<int>(1);
     AMG_CUDA(cudaMemsetAsync(nbig, 0, 2 * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    C.ptr = dev_alloc<int32_t>(m + 1 + kPad);
+    C.ptr = dev_alloc_async<int32_t>(m + 1 + kPad, s);
     AMG_CUDA(cudaMemsetAsync(C.ptr, 0, (m + 1 + kPad) * sizeof(int32_t), s));
 
     const unsigned wgrid = (unsigned)((m + kWarpsPerBlock - 1) / kWarpsPerBlock);
@@ -488,8 +491,8 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
         fail(AMG_ERR_CUDA, "sparse product symbolic phase: hash table overflow");
     }
     C.nnz = nnz;
-    C.col = dev_alloc<int32_t>(nnz + kPad);
-    C.val = dev_alloc<double>(nnz + kPad);
+    C.col = dev_alloc_async<int32_t>(nnz + kPad, s);
+    C.val = dev_alloc_async<double>(nnz + kPad, s);
     AMG_CUDA(cudaMemsetAsync(C.col, 0, (nnz + kPad) * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(C.val, 0, (nnz + kPad) * sizeof(double), s));
     if (m > 0) {
