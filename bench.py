@@ -56,6 +56,62 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+# ------------------------------------------------------- ranks (one per GPU)
+# The single-system solve does not shard (replicas only): every rank solves
+# the whole workload and the job's rate is ranks x steps / slowest rank's
+# time.  The batched and served forms are independent problems: whole systems
+# (requests, grouped by the matrix key they share) are split over the ranks,
+# with no collective on the data path -- only the host-side max of the ranks'
+# times and the gather of per-request latencies.
+def shard_by_weight(weights, world):
+    """Rank of each item: greedy bytes-balanced assignment (heaviest first,
+    each to the least-loaded rank; ties to the lower index and the lower
+    rank), so every rank computes the same assignment without communicating.
+    The heaviest rank exceeds the mean load by at most the heaviest item."""
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    load = [0.0] * world
+    rank_of = [0] * len(weights)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        rank_of[i] = r
+        load[r] += weights[i]
+    return rank_of
+
+
+def shard_requests(reqs, n_of, world):
+    """Rank of each request: requests that share a matrix key stay on one
+    rank (the key's hierarchy is resident there); keys are balanced by the
+    rows their requests solve."""
+    keys = sorted({q.key for q in reqs})
+    w = {k: 0.0 for k in keys}
+    for q in reqs:
+        w[q.key] += n_of(q)
+    rk = dict(zip(keys, shard_by_weight([w[k] for k in keys], world)))
+    return [rk[q.key] for q in reqs]
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest value over the ranks (host-side reduction; CUDA tensors
+    under NCCL, CPU tensors under gloo)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gather_lists(items, world):
+    """Concatenation of every rank's list, in rank order."""
+    if world == 1:
+        return list(items)
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, list(items))
+    return [v for part in out for v in part]
+
+
 # ------------------------------------------------------------ algorithmic bytes
 def kernel_bytes(info):
     """Algorithmic DRAM bytes per launch of each finest-level kernel (FP64 values,
@@ -264,20 +320,31 @@ def cpu_baseline_sample():
 BATCH_SYSTEMS = 4096
 
 
-def bench_batched(amg, torch, dev, stream, args):
+def batched_shard(rank, world):
+    """Indices of the batched workload's systems that this rank solves
+    (bytes-balanced by nonzeros, about 5 n^2 for side n)."""
+    sides, _ = gen.batched_sides(BATCH_SYSTEMS, 0)
+    rank_of = shard_by_weight([5.0 * int(m) ** 2 for m in sides], world)
+    return [k for k in range(BATCH_SYSTEMS) if rank_of[k] == rank]
+
+
+def bench_batched(amg, torch, dev, stream, args, rank=0, world=1):
     """4096 independent 2D Poisson systems (sides U{16..128}, shift U(0,0.1),
     f ~ U(-1,1)), FP32 V-cycle under FP64 CG, rtol 1e-8, one persistent launch
     with the autotuned schedule; against the plain FP64 single-system solve
     (amg_solve per system) timed on an evenly spaced sample of the same
-    systems and scaled to all of them."""
+    systems and scaled to all of them.  With several ranks each solves its
+    shard of the systems and the slowest rank's time counts."""
     sides, sigma = gen.batched_sides(BATCH_SYSTEMS, 0)
-    mats = [gen.poisson2d_shift(int(m), float(sg)) for m, sg in zip(sides, sigma)]
-    rhs = [gen.uniform_pm1(0, 1000 + k, A.n) for k, A in enumerate(mats)]
+    mine = batched_shard(rank, world)
+    nsys = len(mine)
+    mats = [gen.poisson2d_shift(int(sides[k]), float(sigma[k])) for k in mine]
+    rhs = [gen.uniform_pm1(0, 1000 + k, A.n) for k, A in zip(mine, mats)]
     t0 = time.perf_counter()
     b = amg.amg_batch_setup([amg.make_csr(A.n, A.row_ptr, A.col, A.val) for A in mats],
                             amg.amg_params_default(precision=amg.AMG_PRECISION_FP32))
     setup_s = time.perf_counter() - t0
-    tot, off, lev = amg.amg_batch_info(b, BATCH_SYSTEMS)
+    tot, off, lev = amg.amg_batch_info(b, nsys)
     f = torch.from_numpy(np.concatenate(rhs)).to(dev)
     x = torch.zeros(tot, dtype=torch.float64, device=dev)
     threads, ctas = amg.amg_batch_tune(b, f, x, RTOL, MAXITER)
@@ -287,15 +354,15 @@ def bench_batched(amg, torch, dev, stream, args):
         x.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st, it, rr, sst = amg.amg_batch_solve(b, BATCH_SYSTEMS, f, x, RTOL, MAXITER)
+        st, it, rr, sst = amg.amg_batch_solve(b, nsys, f, x, RTOL, MAXITER)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
         assert st == 0 and (rr <= RTOL).all()
     amg.amg_batch_free(b)
-    batch_s = statistics.median(times)
+    batch_s = max_over_ranks(statistics.median(times), world, dev)
     # plain FP64 path: one handle and one solve per system, on a sample
-    sample = list(range(0, BATCH_SYSTEMS, BATCH_SYSTEMS // 128))
+    sample = list(range(0, nsys, max(1, nsys // 128)))
     plain = 0.0
     for k in sample:
         A = mats[k]
@@ -309,14 +376,18 @@ def bench_batched(amg, torch, dev, stream, args):
         S.solve(fk, xk, RTOL, MAXITER)
         plain += time.perf_counter() - t1
         S.close()
-    plain_s = plain * BATCH_SYSTEMS / len(sample)
+    plain_s = max_over_ranks(plain * nsys / len(sample), world, dev)
+    it = np.array(gather_lists([int(v) for v in it], world))
     return {"workload": f"{BATCH_SYSTEMS} x 2D Poisson + shift, sides U{{16..128}}, FP32 V-cycle + FP64 CG",
-            "unknowns": int(tot), "setup_s": setup_s, "solve_s": batch_s,
+            "unknowns": int(sum(gather_lists([int(tot)], world))),
+            "ranks": world, "setup_s": max_over_ranks(setup_s, world, dev), "solve_s": batch_s,
             "value": BATCH_SYSTEMS / batch_s, "unit": "systems/s",
             "iterations_mean": float(np.mean(it)), "iterations_max": int(np.max(it)),
-            "levels_max": int(lev.max()), "schedule": {"threads": threads, "ctas_per_sm": ctas},
+            "levels_max": int(max_over_ranks(lev.max(), world, dev)),
+            "schedule": {"threads": threads, "ctas_per_sm": ctas},
             "plain_fp64_solve_s": plain_s,
-            "plain_note": f"amg_solve per system (FP64, CUDA graph) on {len(sample)} evenly spaced systems, scaled to {BATCH_SYSTEMS}",
+            "plain_note": f"amg_solve per system (FP64, CUDA graph) on {len(sample)} evenly spaced systems"
+                          f" of each rank's {nsys}, scaled to them (slowest rank)",
             "speedup_vs_plain": plain_s / batch_s}
 
 
@@ -340,7 +411,7 @@ def _serve_matrices(reqs):
         return dict(zip(combos, ex.map(make, combos)))
 
 
-def bench_serving(amg, args):
+def bench_serving(amg, args, rank=0, world=1, dev=None):
     """A stream of solve requests through the server: grid sides log-uniform
     on [20, 160] (8,000 to 4,096,000 unknowns), 70% SPD (3D Poisson and
     variable-coefficient diffusion with k = 10^U(-2,2), CG), 30% upwind convection-diffusion
@@ -352,7 +423,10 @@ def bench_serving(amg, args):
     hierarchy kept until its key's last request), then latency under Poisson
     arrivals at 70% of the saturated rate."""
     nreq, slots = args.serve_requests, args.serve_slots
-    reqs = gen.serving_requests(nreq, SEED, lo=20, hi=160)
+    allreq = gen.serving_requests(nreq, SEED, lo=20, hi=160)
+    # with several ranks, each serves the requests of its share of the matrix keys
+    rank_of = shard_requests(allreq, lambda q: q.side ** 3, world)
+    reqs = [q for q in allreq if rank_of[q.index] == rank]
     t0 = time.perf_counter()
     mats = _serve_matrices(reqs)
     gen_s = time.perf_counter() - t0
@@ -361,22 +435,22 @@ def bench_serving(amg, args):
     prm_cg = amg.amg_params_default()
     prm_bi = amg.amg_params_default(solver=amg.AMG_SOLVER_BICGSTAB, smoother=amg.AMG_SMOOTHER_SPAI0)
     prm_of = lambda q: prm_bi if q.solver else prm_cg  # noqa: E731
-    rhs = [q.rhs(SEED, A_of(q).n) for q in reqs]
+    rhs = {q.index: q.rhs(SEED, A_of(q).n) for q in reqs}
     csrs = {c: amg.make_csr(A.n, A.row_ptr, A.col, A.val) for c, A in mats.items()}
     last_use = {q.key: q.index for q in reqs}
-    rows = sum(A_of(q).n for q in reqs)
+    rows = sum(gather_lists([int(sum(A_of(q).n for q in reqs))], world))
 
     # plain API, one request after another
-    handles, serial_status = {}, []
+    handles, serial_status = {}, {}
     t0 = time.perf_counter()
     for q in reqs:
         if q.key not in handles:
             handles[q.key] = amg.amg_setup(csrs[(q.kind, q.side)], prm_of(q))
         x = np.zeros(A_of(q).n)
-        serial_status.append(amg.amg_solve_host(handles[q.key], rhs[q.index], x, RTOL, MAXITER)[0])
+        serial_status[q.index] = amg.amg_solve_host(handles[q.key], rhs[q.index], x, RTOL, MAXITER)[0]
         if last_use[q.key] == q.index:
             amg.amg_free(handles.pop(q.key))
-    serial_s = time.perf_counter() - t0
+    serial_s = max_over_ranks(time.perf_counter() - t0, world, dev)
 
     def run(arrival):
         """Submit every request at its arrival time (None: all at once),
@@ -398,29 +472,35 @@ def bench_serving(amg, args):
         return wall, res, stats
 
     sat_s, sat_res, sat_stats = run(None)
+    sat_s = max_over_ranks(sat_s, world, dev)
     sat_rate = nreq / sat_s
     # Poisson arrivals at 70% of the saturated rate (the stream's seeded draws at rate 1, rescaled)
     rate = 0.7 * sat_rate
     unit_arrivals = np.array([q.arrival for q in gen.serving_requests(nreq, SEED, lo=20, hi=160, rate=1.0)])
     open_s, open_res, open_stats = run(unit_arrivals / rate)
-    lat = np.array([r[4] for r in open_res]) * 1e3
-    ok = all(r[0] == 0 and r[3] <= RTOL for r in sat_res + open_res) and all(s == 0 for s in serial_status)
+    open_s = max_over_ranks(open_s, world, dev)
+    lat = np.array(gather_lists([float(r[4]) for r in open_res], world)) * 1e3
+    ok = all(r[0] == 0 and r[3] <= RTOL for r in sat_res + open_res) and all(s == 0 for s in serial_status.values())
+    ok = all(gather_lists([ok], world))
     failed = [{"index": q.index, "kind": q.kind, "side": q.side, "status": [r[0], o[0], serial_status[q.index]],
                "iters": r[2], "relres": r[3]}
               for q, r, o in zip(reqs, sat_res, open_res)
               if r[0] != 0 or o[0] != 0 or serial_status[q.index] != 0 or r[3] > RTOL][:10]
-    same = all(np.array_equal(a[1], b[1]) for a, b in zip(sat_res, open_res))
+    failed = gather_lists(failed, world)[:10]
+    same = all(gather_lists([all(np.array_equal(a[1], b[1]) for a, b in zip(sat_res, open_res))], world))
     return {"workload": f"{nreq} requests, sides log-uniform [20,160], 70% SPD (CG) / 30% convdiff (BiCGStab), "
                         "20% reuse of an earlier matrix, rtol 1e-8, FP64, host vectors",
-            "requests": nreq, "rows_total": int(rows), "slots": slots, "all_converged": ok, "failed": failed,
+            "requests": nreq, "ranks": world, "rows_total": int(rows), "slots": slots, "all_converged": ok,
+            "failed": failed,
             "same_result_saturated_and_open_loop": same,
             "value": sat_rate, "unit": "requests/s (setup + solve)", "saturated_s": sat_s,
             "serial_plain_s": serial_s, "serial_plain_rate": nreq / serial_s, "speedup_vs_serial": serial_s / sat_s,
             "open_loop_rate": rate, "open_loop_s": open_s,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "peak_charged_bytes": sat_stats["peak_bytes"], "evictions": sat_stats["evictions"],
-            "matrix_generation_s": gen_s}
+            "peak_charged_bytes": int(max_over_ranks(sat_stats["peak_bytes"], world, dev)),
+            "evictions": int(sum(gather_lists([int(sat_stats["evictions"])], world))),
+            "matrix_generation_s": max_over_ranks(gen_s, world, dev)}
 
 
 # ---------------------------------------------------------------------- main
@@ -578,11 +658,11 @@ def main():
 
     batched = None
     if not args.no_batch:
-        batched = bench_batched(amg, torch, dev, stream, args)
+        batched = bench_batched(amg, torch, dev, stream, args, rank, world)
 
     serving = None
     if not args.no_serve:
-        serving = bench_serving(amg, args)
+        serving = bench_serving(amg, args, rank, world, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
