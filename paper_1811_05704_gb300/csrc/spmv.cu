@@ -151,6 +151,36 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+constexpr int kGatherBatch = 8;
+
+// sum -/+ the products of nonzeros k, k + vw, ... < ke, in that order; the
+// columns, values and gathered operands of kGatherBatch nonzeros at a time
+// are loaded before any is accumulated.
+template <int SIGN, typename acc_t, typename VT, typename Epi>
+__device__ __forceinline__ acc_t row_batched(acc_t sum, int k, int ke, int vw, const VT* vs, const int* cs,
+                                             const Epi& epi) {
+    for (; k < ke; k += kGatherBatch * vw) {
+        int c[kGatherBatch];
+        acc_t a[kGatherBatch], x[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const bool in = k + u * vw < ke;
+            c[u] = in ? cs[k + u * vw] : 0;
+            a[u] = in ? (acc_t)vs[k + u * vw] : acc_t(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) x[u] = (k + u * vw < ke) ? epi.xg(c[u]) : acc_t(0);
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            if (k + u * vw < ke) {
+                if constexpr (SIGN < 0) sum -= a[u] * x[u];
+                else sum += a[u] * x[u];
+            }
+        }
+    }
+    return sum;
+}
+
 template <typename VT, typename Epi, int RMAX>
 __global__ void __launch_bounds__(kCons + 32, stream_ctas<VT>())
 k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -320,7 +350,14 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                     }
                     if (active) {
                         const int kb = rp[row - inf.z] - inf.w, ke = rp[row + 1 - inf.z] - inf.w;
-                        if constexpr (Seeding<Epi>::sign < 0) {
+                        if constexpr (!std::is_same<acc_t, double>::value) {
+                            // float32 kernels are bound by gather latency, not
+                            // by a pipe: a lane loads the columns and values
+                            // of up to kGatherBatch of its nonzeros, issues
+                            // their gathers together, then accumulates them
+                            // in order (the same order as one at a time)
+                            sum = row_batched<Seeding<Epi>::sign>(sum, kb + lane, ke, vw, vs, cs, epi);
+                        } else if constexpr (Seeding<Epi>::sign < 0) {
 #pragma unroll 4
                             for (int k = kb + lane; k < ke; k += vw) sum -= (acc_t)vs[k] * epi.xg(cs[k]);
                         } else {
