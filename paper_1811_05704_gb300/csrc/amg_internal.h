@@ -169,7 +169,7 @@ void launch_smooth(const DevCsr& A, const double* d, const double* f, const doub
                    const double* w, const Reduce* r, const int* skip, cudaStream_t s);
 // r = f - A x with dots (r.r, f.f); optional copy of r to r2
 void launch_residual(const DevCsr& A, const double* f, const double* x, double* r, double* r2,
-                     const Reduce& red, const int* skip, cudaStream_t s);
+                     const Reduce& red, const int* skip, cudaStream_t s, float* r32 = nullptr);
 // x += P xc
 void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int* skip,
                         cudaStream_t s);
@@ -189,11 +189,11 @@ void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const in
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s);
 void launch_cg_pupdate(KState* st, const double* z, double* p, int64_t n, cudaStream_t s);
 void launch_cg_update(const Reduce& r, const double* p, const double* q, double* x, double* rv,
-                      int64_t n, cudaStream_t s);
+                      int64_t n, cudaStream_t s, float* r32 = nullptr);
 void launch_bi_pupdate(KState* st, const double* r, const double* v, double* p, int64_t n,
-                       cudaStream_t s);
+                       cudaStream_t s, float* p32 = nullptr);
 void launch_bi_s(const Reduce& red, const double* r, const double* v, double* sv, int64_t n,
-                 cudaStream_t s);
+                 cudaStream_t s, float* s32 = nullptr);
 void launch_bi_update(const Reduce& red, const double* rh, const double* ph, const double* sh,
                       const double* sv, const double* t, double* x, double* rv, int64_t n,
                       cudaStream_t s);

@@ -239,6 +239,12 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
             for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->rh, &h->v, &h->ph, &h->sv, &h->sh,
                                &h->tv, &h->fbuf, &h->xbuf})
                 vec(*v);
+            if (h->prm.precision != AMG_PRECISION_FP64 && h->lev.size() > 1) {
+                h->vin32 = dev_alloc_async<float>(h->n + kPad, h->stream);
+                h->dev_allocs.push_back(h->vin32);
+                h->dev_bytes += (h->n + kPad) * 4;
+                AMG_CUDA(cudaMemsetAsync(h->vin32, 0, (h->n + kPad) * sizeof(float), h->stream));
+            }
             h->st = dev_alloc_async<KState>(1, h->stream);
             h->dev_allocs.push_back(h->st);
             AMG_CUDA(cudaMemsetAsync(h->st, 0, sizeof(KState), h->stream));

@@ -196,8 +196,10 @@ struct EpiSmoothDotF {
     }
 };
 
-// r = f - A x (optionally also into r2), dots r.r and f.f.  f and x may be the
-// caller's buffers, so f is read directly (no shared-memory copy).
+// r = f - A x (optionally also into r2, and with F32 rounded to float32 into
+// r32), dots r.r and f.f.  f and x may be the caller's buffers, so f is read
+// directly (no shared-memory copy).
+template <bool F32>
 struct EpiResid {
     using acc_t = double;
     struct Pre { double f; };
@@ -206,6 +208,7 @@ struct EpiResid {
     const double* __restrict__ x;
     double* __restrict__ r;
     double* __restrict__ r2;
+    float* __restrict__ r32;  // optional: r rounded to float32 (input of a float32 V-cycle)
     __device__ const void* vptr(int) const { return nullptr; }
     __device__ int vbytes(int) const { return 8; }
     __device__ double xg(int c) const { return __ldg(x + c); }
@@ -215,6 +218,7 @@ struct EpiResid {
     __device__ void store(int i, double v, const Pre& p, double& d0, double& d1) const {
         r[i] = v;
         if (r2) r2[i] = v;
+        if constexpr (F32) r32[i] = (float)v;
         d0 = v * v;
         d1 = p.f * p.f;
     }
@@ -251,23 +255,35 @@ struct EpiY32 {
     __device__ void store(int r, float s, const Pre&, double&, double&) const { y[r] = s; }
 };
 
+// F64: the level's right-hand side is the float64 Krylov vector (finest
+// level), else a float32 level vector.  The choice is a template parameter so
+// that the kernels of the other levels contain no float64 conversion at all
+// (on GB300 a conversion from float64 occupies the float64 pipe like a
+// multiply-add).
+template <bool F64>
 struct EpiPre32 {  // as EpiPre, with matrix values a_ij d_j in float32
     using acc_t = float;
     struct Pre { float d, f; };
     static constexpr int ndot = 0, nvec = 2;
     const float* __restrict__ d;
-    const float* __restrict__ f32;   // level rhs (levels >= 1)
-    const double* __restrict__ f64;  // finest-level rhs, or null
+    const float* __restrict__ f32;   // level rhs (F64 false)
+    const double* __restrict__ f64;  // finest-level rhs (F64 true)
     float* __restrict__ x;
     float* __restrict__ t;
     __device__ const void* vptr(int k) const {
-        return k == 0 ? (const void*)d : (f64 ? (const void*)f64 : (const void*)f32);
+        if (k == 0) return d;
+        if constexpr (F64) return f64;
+        else return f32;
     }
-    __device__ int vbytes(int k) const { return (k == 1 && f64) ? 8 : 4; }
-    __host__ __device__ static constexpr int vslot(int k) { return k == 1 ? 8 : 4; }
-    __device__ float xg(int c) const { return f64 ? (float)__ldg(f64 + c) : __ldg(f32 + c); }
+    __device__ int vbytes(int k) const { return (k == 1 && F64) ? 8 : 4; }
+    __host__ __device__ static constexpr int vslot(int k) { return (k == 1 && F64) ? 8 : 4; }
+    __device__ float xg(int c) const {
+        if constexpr (F64) return (float)__ldg(f64 + c);
+        else return __ldg(f32 + c);
+    }
     __device__ Pre load(int r, const VecTile& v) const {
-        return {v.at<float>(0, r), f64 ? (float)v.at<double>(1, r) : v.at<float>(1, r)};
+        if constexpr (F64) return {v.at<float>(0, r), (float)v.at<double>(1, r)};
+        else return {v.at<float>(0, r), v.at<float>(1, r)};
     }
     __device__ void store(int r, float s, const Pre& p, double&, double&) const {
         x[r] = p.d * p.f;
@@ -275,7 +291,10 @@ struct EpiPre32 {  // as EpiPre, with matrix values a_ij d_j in float32
     }
 };
 
-template <bool DOT>
+// F64IN: the right-hand side is the float64 Krylov vector; F64OUT: the output
+// is written in float64 (the finest level's z); otherwise float32 level
+// vectors (see EpiPre32 for why these are template parameters).
+template <bool DOT, bool F64IN, bool F64OUT>
 struct EpiSmooth32 {
     using acc_t = float;
     struct Pre { float x, d, f; double w; };
@@ -284,27 +303,34 @@ struct EpiSmooth32 {
     const float* __restrict__ f32;
     const double* __restrict__ f64;
     const float* __restrict__ x;
-    float* __restrict__ y32;   // level output (levels >= 1)
-    double* __restrict__ y64;  // finest-level output, or null
+    float* __restrict__ y32;   // level output (F64OUT false)
+    double* __restrict__ y64;  // finest-level output (F64OUT true)
     const double* __restrict__ w;
     __device__ const void* vptr(int k) const {
-        return k == 0 ? (const void*)x
-             : k == 1 ? (const void*)d
-             : k == 2 ? (f64 ? (const void*)f64 : (const void*)f32)
-                      : (const void*)w;
+        if (k == 0) return x;
+        if (k == 1) return d;
+        if (k == 2) {
+            if constexpr (F64IN) return f64;
+            else return f32;
+        }
+        return w;
     }
-    __device__ int vbytes(int k) const { return (k == 3 || (k == 2 && f64)) ? 8 : 4; }
-    __host__ __device__ static constexpr int vslot(int k) { return k < 2 ? 4 : 8; }
+    __device__ int vbytes(int k) const { return (k == 3 || (k == 2 && F64IN)) ? 8 : 4; }
+    __host__ __device__ static constexpr int vslot(int k) { return (k == 3 || (k == 2 && F64IN)) ? 8 : 4; }
     __device__ float xg(int c) const { return __ldg(x + c); }
     __device__ Pre load(int r, const VecTile& v) const {
-        return {v.at<float>(0, r), v.at<float>(1, r),
-                f64 ? (float)v.at<double>(2, r) : v.at<float>(2, r), DOT ? v.at<double>(3, r) : 0.0};
+        float f;
+        if constexpr (F64IN) f = (float)v.at<double>(2, r);
+        else f = v.at<float>(2, r);
+        double w = 0.0;
+        if constexpr (DOT) w = v.at<double>(3, r);
+        return {v.at<float>(0, r), v.at<float>(1, r), f, w};
     }
     __device__ void store(int r, float s, const Pre& p, double& d0, double&) const {
         const float val = p.x + p.d * (p.f - s);
-        if (y64) y64[r] = (double)val;
+        if constexpr (F64OUT) y64[r] = (double)val;
         else y32[r] = val;
-        if (DOT) d0 = p.w * (double)val;
+        if constexpr (DOT) d0 = p.w * (double)val;
     }
 };
 

@@ -64,6 +64,10 @@ struct amg_handle {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rh = nullptr, *v = nullptr,
            *ph = nullptr, *sv = nullptr, *sh = nullptr, *tv = nullptr, *fbuf = nullptr,
            *xbuf = nullptr;
+    // float32 V-cycles: the preconditioner's input rounded to float32, written
+    // by the kernel that produces the input (r for CG, p and s for BiCGStab);
+    // null for a float64 V-cycle or a one-level hierarchy
+    float* vin32 = nullptr;
     amg::KState* st = nullptr;        // device
     amg::KState* st_in = nullptr;     // pinned host
     amg::KState* st_out = nullptr;    // pinned host

@@ -396,8 +396,13 @@ static void issue_vcycle64(amg_handle* h, Issue& I, const double* r, double* z, 
 
 // float32 V-cycle (one pre- and one post-sweep); the finest level reads r and
 // writes z in float64, and r.z is reduced in float64.
-static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
-                           const Reduce* rz) {
+// r32, if given, is r rounded to float32 (written by the kernel that produced
+// r): the finest level then reads it instead of converting r's entries at
+// every use -- seven gathers per entry on a 7-point stencil, each conversion
+// from float64 an instruction of GB300's narrow float64 pipe.  The result is
+// the same either way (the kernels round r to float32 before using it).
+static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, const float* r32, double* z,
+                           const int* skip, const Reduce* rz) {
     std::vector<Level>& L = h->lev;
     const int nl = (int)L.size();
     cudaStream_t s = I.s;
@@ -408,7 +413,7 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
         const int kcp = l == 0 ? AMG_KC_PRESMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
         const int kcr = l == 0 ? AMG_KC_RESTRICT_L0 : AMG_KC_VCYCLE_COARSER;
         I.pre(kcp);
-        launch_presmooth_residual_f32(v.A, v.d32, l == 0 ? nullptr : v.f32, l == 0 ? r : nullptr,
+        launch_presmooth_residual_f32(v.A, v.d32, l == 0 ? r32 : v.f32, (l == 0 && !r32) ? r : nullptr,
                                       v.x32, v.t32, skip, s);
         I.post();
         I.pre(kcr); launch_spmv_f32(v.R, v.t32, L[l + 1].f32, skip, s); I.post();
@@ -428,7 +433,7 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
         const int kcs = l == 0 ? AMG_KC_POSTSMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
         I.pre(kc); launch_prolong_add_f32(v.P, below, v.x32, skip, s); I.post();
         I.pre(kcs);
-        launch_smooth_f32(v.A, v.d32, l == 0 ? nullptr : v.f32, l == 0 ? r : nullptr, v.x32,
+        launch_smooth_f32(v.A, v.d32, l == 0 ? r32 : v.f32, (l == 0 && !r32) ? r : nullptr, v.x32,
                           l == 0 ? nullptr : v.y32, l == 0 ? z : nullptr,
                           (l == 0 && rz) ? r : nullptr, l == 0 ? rz : nullptr, skip, s);
         I.post();
@@ -436,9 +441,9 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, double* z, 
     }
 }
 
-static void issue_vcycle(amg_handle* h, Issue& I, const double* r, double* z, const int* skip,
-                         const Reduce* rz) {
-    if (h->prm.precision != AMG_PRECISION_FP64) issue_vcycle32(h, I, r, z, skip, rz);
+static void issue_vcycle(amg_handle* h, Issue& I, const double* r, const float* r32, double* z,
+                         const int* skip, const Reduce* rz) {
+    if (h->prm.precision != AMG_PRECISION_FP64) issue_vcycle32(h, I, r, r32, z, skip, rz);
     else issue_vcycle64(h, I, r, z, skip, rz);
 }
 
@@ -461,7 +466,7 @@ static Reduce with(Reduce r, int fin) {
 // p.q), x += alpha p, r -= alpha q (with r.r and the loop test).
 static void cg_init(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
     const DevCsr& A = h->lev[0].A;
-    I.pre(AMG_KC_OTHER); launch_residual(A, f, x, h->r, nullptr, with(b, FIN_INIT), nullptr, I.s); I.post();
+    I.pre(AMG_KC_OTHER); launch_residual(A, f, x, h->r, nullptr, with(b, FIN_INIT), nullptr, I.s, h->vin32); I.post();
     I.pre(AMG_KC_OTHER); launch_fill(h->p, 0.0, h->n, I.s); I.post();
 }
 
@@ -469,10 +474,10 @@ static void cg_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
     const DevCsr& A = h->lev[0].A;
     const int* halt = flag_ptr(h, offsetof(KState, halt));
     const Reduce rz = with(b, FIN_CG_RHO);
-    issue_vcycle(h, I, h->r, h->z, halt, &rz);
+    issue_vcycle(h, I, h->r, h->vin32, h->z, halt, &rz);
     I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_pupdate(h->st, h->z, h->p, h->n, I.s); I.post();
     I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot(A, h->p, nullptr, h->q, with(b, FIN_CG_ALPHA), halt, I.s); I.post();
-    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_update(with(b, FIN_CG_RES), h->p, h->q, x, h->r, h->n, I.s); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_update(with(b, FIN_CG_RES), h->p, h->q, x, h->r, h->n, I.s, h->vin32); I.post();
 }
 
 // BiCGStab (van der Vorst; right-preconditioned, Saad Alg. 7.7).
@@ -487,11 +492,11 @@ static void bi_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
     const DevCsr& A = h->lev[0].A;
     const int* halt = flag_ptr(h, offsetof(KState, halt));
     const int* skip2 = flag_ptr(h, offsetof(KState, skip2));
-    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_pupdate(h->st, h->r, h->v, h->p, h->n, I.s); I.post();
-    issue_vcycle(h, I, h->p, h->ph, halt, nullptr);
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_pupdate(h->st, h->r, h->v, h->p, h->n, I.s, h->vin32); I.post();
+    issue_vcycle(h, I, h->p, h->vin32, h->ph, halt, nullptr);
     I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot(A, h->ph, h->rh, h->v, with(b, FIN_BI_ALPHA), halt, I.s); I.post();
-    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_s(with(b, FIN_BI_HALF), h->r, h->v, h->sv, h->n, I.s); I.post();
-    issue_vcycle(h, I, h->sv, h->sh, skip2, nullptr);
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_bi_s(with(b, FIN_BI_HALF), h->r, h->v, h->sv, h->n, I.s, h->vin32); I.post();
+    issue_vcycle(h, I, h->sv, h->vin32, h->sh, skip2, nullptr);
     I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot2(A, h->sh, h->sv, h->tv, with(b, FIN_BI_OMEGA), skip2, I.s); I.post();
     I.pre(AMG_KC_KRYLOV_UPDATE);
     launch_bi_update(with(b, FIN_BI_RES), h->rh, h->ph, h->sh, h->sv, h->tv, x, h->r, h->n, I.s);
@@ -707,7 +712,7 @@ void run_vcycle(amg_handle* h, const double* r, double* z) {
     I.s = h->stream;
     // the V-cycle streams row slices of its input: take it from a padded buffer
     AMG_CUDA(cudaMemcpyAsync(h->r, r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    issue_vcycle(h, I, h->r, z, nullptr, nullptr);
+    issue_vcycle(h, I, h->r, nullptr, z, nullptr, nullptr);
     AMG_CUDA(cudaStreamSynchronize(h->stream));
 }
 

@@ -603,8 +603,9 @@ void launch_smooth(const DevCsr& A, const double* d, const double* f, const doub
 }
 
 void launch_residual(const DevCsr& A, const double* f, const double* x, double* r, double* r2,
-                     const Reduce& red, const int* skip, cudaStream_t s) {
-    run(A, A.val, EpiResid{f, x, r, r2}, red, skip, s);
+                     const Reduce& red, const int* skip, cudaStream_t s, float* r32) {
+    if (r32) run(A, A.val, EpiResid<true>{f, x, r, r2, r32}, red, skip, s);
+    else run(A, A.val, EpiResid<false>{f, x, r, r2, nullptr}, red, skip, s);
 }
 
 void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int* skip,
@@ -630,14 +631,32 @@ void launch_spmv_f32(const DevCsr& A, const float* x, float* y, const int* skip,
 void launch_presmooth_residual_f32(const DevCsr& A, const float* d, const float* f32,
                                    const double* f64, float* x, float* t, const int* skip,
                                    cudaStream_t s) {
-    run32(A, A.vald32, A.vald16, EpiPre32{d, f32, f64, x, t}, Reduce{}, skip, s);
+    if (f64) run32(A, A.vald32, A.vald16, EpiPre32<true>{d, nullptr, f64, x, t}, Reduce{}, skip, s);
+    else run32(A, A.vald32, A.vald16, EpiPre32<false>{d, f32, nullptr, x, t}, Reduce{}, skip, s);
+}
+
+template <bool DOT>
+static void smooth_f32(const DevCsr& A, const EpiSmooth32<DOT, false, false>& e, const Reduce& r,
+                       const int* skip, cudaStream_t s) {
+    // the float64 input and output, where given, select the instantiation
+    if (e.f64 && e.y64)
+        run32(A, A.val32, A.val16, EpiSmooth32<DOT, true, true>{e.d, nullptr, e.f64, e.x, nullptr, e.y64, e.w}, r,
+              skip, s);
+    else if (e.f64)
+        run32(A, A.val32, A.val16, EpiSmooth32<DOT, true, false>{e.d, nullptr, e.f64, e.x, e.y32, nullptr, e.w}, r,
+              skip, s);
+    else if (e.y64)
+        run32(A, A.val32, A.val16, EpiSmooth32<DOT, false, true>{e.d, e.f32, nullptr, e.x, nullptr, e.y64, e.w}, r,
+              skip, s);
+    else
+        run32(A, A.val32, A.val16, e, r, skip, s);
 }
 
 void launch_smooth_f32(const DevCsr& A, const float* d, const float* f32, const double* f64,
                        const float* x, float* y32, double* y64, const double* w,
                        const Reduce* r, const int* skip, cudaStream_t s) {
-    if (r) run32(A, A.val32, A.val16, EpiSmooth32<true>{d, f32, f64, x, y32, y64, w}, *r, skip, s);
-    else run32(A, A.val32, A.val16, EpiSmooth32<false>{d, f32, f64, x, y32, y64, nullptr}, Reduce{}, skip, s);
+    if (r) smooth_f32<true>(A, EpiSmooth32<true, false, false>{d, f32, f64, x, y32, y64, w}, *r, skip, s);
+    else smooth_f32<false>(A, EpiSmooth32<false, false, false>{d, f32, f64, x, y32, y64, nullptr}, Reduce{}, skip, s);
 }
 
 void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const int* skip,
@@ -679,9 +698,13 @@ __global__ void k_cg_pupdate(const KState* __restrict__ st, const double* __rest
         p[i] = z[i] + beta * p[i];
 }
 
+// F32: also write the updated vector rounded to float32 (the input of a
+// float32 V-cycle); a template parameter, so that the float64 solve's kernel
+// has no conversion on its float64 pipe.
+template <bool F32>
 __global__ void __launch_bounds__(kThreads)
 k_cg_update(Reduce red, const double* __restrict__ p, const double* __restrict__ q,
-            double* __restrict__ x, double* __restrict__ r, int64_t n) {
+            double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32, int64_t n) {
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
     double acc = 0.0;
@@ -690,23 +713,30 @@ k_cg_update(Reduce red, const double* __restrict__ p, const double* __restrict__
         x[i] += alpha * p[i];
         const double v = r[i] - alpha * q[i];
         r[i] = v;
+        if constexpr (F32) r32[i] = (float)v;
         acc += v * v;
     }
     reduce_finalize(red, acc, 0.0);
 }
 
+template <bool F32>  // as k_cg_update
 __global__ void k_bi_pupdate(const KState* __restrict__ st, const double* __restrict__ r,
-                             const double* __restrict__ v, double* __restrict__ p, int64_t n) {
+                             const double* __restrict__ v, double* __restrict__ p, float* __restrict__ p32,
+                             int64_t n) {
     if (st->halt) return;
     const double beta = st->beta, omega = st->omega;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = r[i] + beta * (p[i] - omega * v[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double pv = r[i] + beta * (p[i] - omega * v[i]);
+        p[i] = pv;
+        if constexpr (F32) p32[i] = (float)pv;
+    }
 }
 
+template <bool F32>  // as k_cg_update
 __global__ void __launch_bounds__(kThreads)
 k_bi_s(Reduce red, const double* __restrict__ r, const double* __restrict__ v,
-       double* __restrict__ sv, int64_t n) {
+       double* __restrict__ sv, float* __restrict__ s32, int64_t n) {
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
     double acc = 0.0;
@@ -714,6 +744,7 @@ k_bi_s(Reduce red, const double* __restrict__ r, const double* __restrict__ v,
          i += (int64_t)gridDim.x * blockDim.x) {
         const double s = r[i] - alpha * v[i];
         sv[i] = s;
+        if constexpr (F32) s32[i] = (float)s;
         acc += s * s;
     }
     reduce_finalize(red, acc, 0.0);
@@ -831,20 +862,23 @@ void launch_cg_pupdate(KState* st, const double* z, double* p, int64_t n, cudaSt
 }
 
 void launch_cg_update(const Reduce& r, const double* p, const double* q, double* x, double* rv,
-                      int64_t n, cudaStream_t s) {
-    k_cg_update<<<vec_grid(n), kThreads, 0, s>>>(r, p, q, x, rv, n);
+                      int64_t n, cudaStream_t s, float* r32) {
+    if (r32) k_cg_update<true><<<vec_grid(n), kThreads, 0, s>>>(r, p, q, x, rv, r32, n);
+    else k_cg_update<false><<<vec_grid(n), kThreads, 0, s>>>(r, p, q, x, rv, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_bi_pupdate(KState* st, const double* r, const double* v, double* p, int64_t n,
-                       cudaStream_t s) {
-    k_bi_pupdate<<<vec_grid(n), kThreads, 0, s>>>(st, r, v, p, n);
+                       cudaStream_t s, float* p32) {
+    if (p32) k_bi_pupdate<true><<<vec_grid(n), kThreads, 0, s>>>(st, r, v, p, p32, n);
+    else k_bi_pupdate<false><<<vec_grid(n), kThreads, 0, s>>>(st, r, v, p, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_bi_s(const Reduce& red, const double* r, const double* v, double* sv, int64_t n,
-                 cudaStream_t s) {
-    k_bi_s<<<vec_grid(n), kThreads, 0, s>>>(red, r, v, sv, n);
+                 cudaStream_t s, float* s32) {
+    if (s32) k_bi_s<true><<<vec_grid(n), kThreads, 0, s>>>(red, r, v, sv, s32, n);
+    else k_bi_s<false><<<vec_grid(n), kThreads, 0, s>>>(red, r, v, sv, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 

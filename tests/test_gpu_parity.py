@@ -346,6 +346,34 @@ def test_mixed_vcycle_reaches_fp64_tolerance(amg, torch_dev, precision):
         S.close()
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_vcycle_bicgstab(amg, torch_dev, precision):
+    """BiCGStab with the float32 V-cycle (whose finest level reads the float32
+    copies of p and s that the Krylov kernels write) on a nonsymmetric
+    convection-diffusion system: the FP64 tolerance is reached, x within 1e-6
+    of the FP64 oracle's BiCGStab solution."""
+    import oracle
+    A = gen.convdiff3d(18, seed=2)[0]
+    kw = {"solver": 1, "smoother": 1, "coarse_enough": 100}
+    f, _ = gen.rhs_from_solution(A, 9)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=precision, **kw)
+    x = t(torch_dev, np.zeros(A.n))
+    st, it, rr = S.solve(t(torch_dev, f), x, rtol=1e-8, maxiter=300)
+    xs = x.cpu().numpy()
+    H = oracle.Hierarchy(A, params=orc_params(**kw))
+    xo, ito, rro, sto = H.bicgstab(f, rtol=1e-8, maxiter=300)
+    assert sto == 0 and st == 0 and rr <= 1e-8 and _true_relres(A, xs, f) <= 1e-8
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert it <= ito + MIXED_SLACK[precision], (it, ito)
+    # the host-driven launches take the same float32 copies: same result
+    S2 = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=precision, use_graph=0, **kw)
+    x2 = t(torch_dev, np.zeros(A.n))
+    st2, it2, rr2 = S2.solve(t(torch_dev, f), x2, rtol=1e-8, maxiter=300)
+    assert (st2, it2) == (st, it) and np.array_equal(x2.cpu().numpy(), xs)
+    S.close()
+    S2.close()
+
+
 def test_full_size_poisson150(amg, torch_dev):
     """The 150^3 workload the benchmark times: hierarchy sizes and sampled
     rows against the oracle, the solve against the oracle's solve."""
