@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "batch.h"
 #include "device_common.cuh"
@@ -30,19 +31,41 @@ __device__ __forceinline__ double block_allsum(double v, double* sh) {
     return t;
 }
 
-// row i of a CSR matrix times a gathered vector
+// row i of a CSR matrix times a gathered vector, summed in column order.  The
+// columns and values of up to kRowBatch nonzeros are loaded, then their
+// operands gathered, before any is accumulated: a short row costs one
+// dependent round trip per step instead of one per nonzero.
+constexpr int kRowBatch = 8;
 template <typename VT, typename XT, typename AT>
 __device__ __forceinline__ AT row_dot(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                       const VT* __restrict__ val, const XT* __restrict__ x, int i) {
+    const int kb = ptr[i], ke = ptr[i + 1];
     AT s = AT(0);
-    for (int k = ptr[i]; k < ptr[i + 1]; ++k) s += (AT)val[k] * (AT)x[col[k]];
+    for (int k = kb; k < ke; k += kRowBatch) {
+        int c[kRowBatch];
+        AT a[kRowBatch], g[kRowBatch];
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+            const bool in = k + u < ke;
+            c[u] = in ? col[k + u] : 0;
+            a[u] = in ? (AT)val[k + u] : AT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) g[u] = (k + u < ke) ? (AT)x[c[u]] : AT(0);
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u)
+            if (k + u < ke) s += a[u] * g[u];
+    }
     return s;
 }
 
 // z = M r (one V-cycle, zero initial guess on every level) and returns the
-// block-wide r.z.  T is the V-cycle type; r and z are float64.
+// block-wide r.z.  T is the V-cycle type; r and z are float64.  rT is r in
+// the V-cycle type (float32: r rounded once by the kernel step that wrote r,
+// so that the finest level does not convert r's entries at every gather).
 template <typename T>
-__device__ double vcycle_block(const BSys& S, const double* __restrict__ r, double* __restrict__ z, double* sh) {
+__device__ double vcycle_block(const BSys& S, const double* __restrict__ r, const T* __restrict__ rT,
+                               double* __restrict__ z, double* sh) {
     const int L = S.nlev;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -65,8 +88,8 @@ __device__ double vcycle_block(const BSys& S, const double* __restrict__ r, doub
         T* t = static_cast<T*>(v.t);
         if (l == 0) {
             for (int i = tid; i < v.n; i += nt) {
-                const T s = row_dot<T, double, T>(v.Aptr, v.Acol, vald, r, i);
-                const T fi = (T)r[i];
+                const T s = row_dot<T, T, T>(v.Aptr, v.Acol, vald, rT, i);
+                const T fi = rT[i];
                 x[i] = d[i] * fi;
                 t[i] = fi - s;
             }
@@ -111,7 +134,7 @@ __device__ double vcycle_block(const BSys& S, const double* __restrict__ r, doub
         if (l == 0) {
             for (int i = tid; i < v.n; i += nt) {
                 const T s = row_dot<T, T, T>(v.Aptr, v.Acol, av, x, i);
-                const double zi = (double)(x[i] + d[i] * ((T)r[i] - s));
+                const double zi = (double)(x[i] + d[i] * (rT[i] - s));
                 z[i] = zi;
                 rz += r[i] * zi;
             }
@@ -138,11 +161,22 @@ __device__ void cg_block(const BSys& S, const double* __restrict__ f, double* __
     double* z = S.z;
     double* p = S.p;
     double* q = S.q;
+    // r in the V-cycle type, written wherever r is: for a float32 V-cycle the
+    // finest level's y (unused on that level), else r itself
+    T* rT = nullptr;
+    if constexpr (std::is_same<T, double>::value) rT = r;
+    else if (S.nlev > 1) rT = static_cast<T*>(S.lev[0].y);
+    auto put = [&](int i, double v) {
+        r[i] = v;
+        if constexpr (!std::is_same<T, double>::value) {
+            if (rT) rT[i] = (T)v;
+        }
+    };
     // r = f - A x, ||r||, ||f||
     double a = 0.0, b = 0.0;
     for (int i = tid; i < n; i += nt) {
         const double v = f[i] - row_dot<double, double, double>(S.ptr, S.col, S.val, x, i);
-        r[i] = v;
+        put(i, v);
         a += v * v;
         b += f[i] * f[i];
     }
@@ -164,7 +198,7 @@ __device__ void cg_block(const BSys& S, const double* __restrict__ f, double* __
         double res_k = relres, rho = 0.0;
         bool first = true;
         while (res_k > rtol && it < maxiter) {
-            const double rho_new = vcycle_block<T>(S, r, z, sh);
+            const double rho_new = vcycle_block<T>(S, r, rT, z, sh);
             if (!(rho_new > 0.0) || !isfinite(rho_new)) { status = AMG_ERR_BREAKDOWN; break; }
             const double beta = first ? 0.0 : rho_new / rho;
             rho = rho_new;
@@ -187,7 +221,7 @@ __device__ void cg_block(const BSys& S, const double* __restrict__ f, double* __
             for (int i = tid; i < n; i += nt) {
                 x[i] += alpha * p[i];
                 const double v = r[i] - alpha * q[i];
-                r[i] = v;
+                put(i, v);
                 s2 += v * v;
             }
             res_k = sqrt(block_allsum(s2, sh)) / nf;
@@ -197,7 +231,7 @@ __device__ void cg_block(const BSys& S, const double* __restrict__ f, double* __
         double t2 = 0.0;
         for (int i = tid; i < n; i += nt) {
             const double v = f[i] - row_dot<double, double, double>(S.ptr, S.col, S.val, x, i);
-            r[i] = v;
+            put(i, v);
             t2 += v * v;
         }
         relres = sqrt(block_allsum(t2, sh)) / nf;
