@@ -131,18 +131,19 @@ def kernel_bytes(info):
 
 def kernel_bytes_mixed(info, vb):
     """As kernel_bytes for the float32 V-cycle with vb-byte matrix values (4:
-    float32, 2: bfloat16): float32 level vectors, except the finest level's
-    float64 residual input and correction output."""
+    float32, 2: bfloat16): float32 level vectors; the finest level reads the
+    Krylov vector as the float32 copy the Krylov kernels write, and writes z
+    in float64 with the float64 dot product r.z."""
     n0, z0 = info["rows"][0], info["nnz"][0]
     n1 = info["rows"][1] if info["levels"] > 1 else 0
     zp = info["nnz_p"][0]
     e = vb + 4
     return {
         "spmv_dot": 12 * z0 + 4 * n0 + 8 * n0 + 8 * n0,       # FP64, as kernel_bytes
-        "presmooth_l0": e * z0 + 4 * n0 + 12 * n0 + 8 * n0,   # A, d (f32) r (f64) read, x t (f32) written
+        "presmooth_l0": e * z0 + 4 * n0 + 8 * n0 + 8 * n0,    # A, d r (f32) read, x t (f32) written
         "restrict_l0": e * zp + 4 * n1 + 4 * n0 + 4 * n1,     # R, t, f_1
         "prolong_l0": e * zp + 4 * n0 + 4 * n1 + 8 * n0,      # P, x_1, x read+write
-        "postsmooth_l0": e * z0 + 4 * n0 + 4 * n0 + 12 * n0 + 8 * n0,  # A, x, d r, z (f64)
+        "postsmooth_l0": e * z0 + 4 * n0 + 4 * n0 + 8 * n0 + 8 * n0 + 8 * n0,  # A, x, d r (f32), r (f64), z (f64)
     }
 
 
