@@ -11,6 +11,7 @@
 #include "amg_internal.h"
 #include "batch.h"
 #include "handle.h"
+#include "host_parallel.h"
 
 namespace amg {
 
@@ -210,8 +211,17 @@ amg_status amg_setup(const amg_csr* A, const amg_params* prm, void* stream, amg_
         H.nrows = H.ncols = A->n;
         H.ptr.resize(A->n + 1);
         auto fetch = [&](void* dst, const void* src, size_t bytes) {
-            if (A->on_device) AMG_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
-            else std::memcpy(dst, src, bytes);
+            if (A->on_device) {
+                AMG_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+                return;
+            }
+            // host input: copied in parallel chunks (a large matrix is
+            // hundreds of MB)
+            const int64_t C = row_chunks((int64_t)(bytes / 8), (int64_t)(bytes / 8));
+            parallel_for(C, [&](int64_t c) {
+                const size_t lo = bytes * c / C, hi = bytes * (c + 1) / C;
+                std::memcpy(static_cast<char*>(dst) + lo, static_cast<const char*>(src) + lo, hi - lo);
+            });
         };
         fetch(H.ptr.data(), A->row_ptr, (A->n + 1) * sizeof(int32_t));
         if (H.ptr[A->n] != A->nnz) fail(AMG_ERR_INVALID_ARG, "row_ptr[n] != nnz");

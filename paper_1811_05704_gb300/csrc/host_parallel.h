@@ -16,10 +16,18 @@
 
 namespace amg {
 
-// Host threads for one parallel step (at most 16).
+// Cap on the threads of one parallel step for the calling thread (0: none).
+// A server worker sets it to its share of the cores, so that several
+// set-ups running at once do not oversubscribe the host.
+inline thread_local unsigned t_thread_cap = 0;
+
+// Host threads for one parallel step (at most 16, and at most the calling
+// thread's cap).
 inline unsigned host_threads() {
     const unsigned hw = std::thread::hardware_concurrency();
-    return std::max(1u, std::min(16u, hw ? hw : 1u));
+    unsigned n = std::max(1u, std::min(16u, hw ? hw : 1u));
+    if (t_thread_cap) n = std::min(n, t_thread_cap);
+    return n;
 }
 
 // Run fn(i) for i in [0, n) on host_threads() threads; rethrows the first
@@ -49,23 +57,30 @@ void parallel_for(int64_t n, F&& fn) {
     if (err) std::rethrow_exception(err);
 }
 
-// Number of chunks for n rows: one per 65,536 rows, at most 64, so small
-// matrices (and the many small systems of the batched set-up, which already
-// run one system per thread) stay on the calling thread.
-inline int row_chunks(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(64, n / 65536));
+// Number of chunks for n rows holding `work` nonzeros: one per 65,536 rows
+// or per 262,144 nonzeros, whichever gives more (coarse levels have few rows
+// of many nonzeros), at most 64 and at most n; small matrices (and the many
+// small systems of the batched set-up, which already run one system per
+// thread) stay on the calling thread.
+inline int row_chunks(int64_t n, int64_t work = 0) {
+    const int64_t c = std::max<int64_t>(n / 65536, work / 262144);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(64, c), n));
 }
 
 // fn(c, lo, hi) for the chunks c of [0, n): chunk c is
-// [n c / C, n (c + 1) / C) with C = row_chunks(n).
+// [n c / C, n (c + 1) / C) with C = row_chunks(n, work).
 template <class F>
-void parallel_rows(int64_t n, F&& fn) {
-    const int C = row_chunks(n);
+void parallel_rows(int64_t n, int64_t work, F&& fn) {
+    const int C = row_chunks(n, work);
     if (C == 1) {
         fn(0, (int64_t)0, n);
         return;
     }
     parallel_for(C, [&](int64_t c) { fn((int)c, n * c / C, n * (c + 1) / C); });
+}
+template <class F>
+void parallel_rows(int64_t n, F&& fn) {
+    parallel_rows(n, (int64_t)0, fn);
 }
 
 }  // namespace amg

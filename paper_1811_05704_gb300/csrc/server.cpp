@@ -15,6 +15,7 @@
 // launch shapes, fixed-order reductions), so a result is the same alone and
 // in the mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -26,6 +27,7 @@
 
 #include "amg_internal.h"
 #include "handle.h"
+#include "host_parallel.h"
 
 namespace amg {
 
@@ -89,6 +91,7 @@ struct amg_server {
     int64_t completed = 0;
     int64_t evictions = 0;
     int running = 0;
+    std::atomic<int> setups{0};  // set-ups running now (their host steps share the cores)
     bool stop = false;
     std::vector<std::thread> workers;
 };
@@ -213,6 +216,11 @@ void worker(amg_server* s) {
             c.col = r->A.col.data();
             c.val = r->A.val.data();
             c.on_device = 0;
+            // the host steps of this set-up use its share of the cores among
+            // the set-ups running now (all of them when it runs alone)
+            const int sharing = ++s->setups;
+            const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+            t_thread_cap = std::max(1u, hw / (unsigned)sharing);
             status = amg_setup(&c, &r->prm, st, &h);
             if (status == AMG_ERR_OOM) {
                 // the charge underestimated this hierarchy or other memory is
@@ -231,6 +239,7 @@ void worker(amg_server* s) {
                 for (amg_handle* e : idle) amg_free(e);
                 if (!idle.empty()) status = amg_setup(&c, &r->prm, st, &h);
             }
+            --s->setups;
             if (status != AMG_OK) err = amg_last_error();
         } else {
             h->stream = st;  // run on this slot's stream

@@ -29,9 +29,9 @@ void host_validate(const HostCsr& A) {
     if ((int64_t)A.ptr[A.nrows] > (int64_t)A.col.size() || (int64_t)A.ptr[A.nrows] > (int64_t)A.val.size())
         fail(AMG_ERR_INVALID_ARG, "row_ptr[n] exceeds the column and value arrays");
     // the first bad row of each chunk; the lowest over the chunks is reported
-    std::vector<int64_t> bad(row_chunks(A.nrows), -1);
+    std::vector<int64_t> bad(row_chunks(A.nrows, A.ptr[A.nrows]), -1);
     std::vector<int> why(bad.size(), 0);
-    parallel_rows(A.nrows, [&](int c, int64_t lo, int64_t hi) {
+    parallel_rows(A.nrows, A.ptr[A.nrows], [&](int c, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi && bad[c] < 0; ++i)
             for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
                 int w = 0;
@@ -52,7 +52,7 @@ void host_validate(const HostCsr& A) {
 
 std::vector<double> host_diagonal(const HostCsr& A) {
     std::vector<double> dg(A.nrows, 0.0);
-    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+    parallel_rows(A.nrows, A.nnz(), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i) {
             const int32_t* b = A.col.data() + A.ptr[i];
             const int32_t* e = A.col.data() + A.ptr[i + 1];
@@ -73,7 +73,7 @@ namespace {
 std::vector<uint8_t> strong_mask(const HostCsr& A, const std::vector<double>& dg, double eps) {
     const double e2 = eps * eps;
     std::vector<uint8_t> s(A.nnz(), 0);
-    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+    parallel_rows(A.nrows, A.nnz(), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i)
             for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
                 const int32_t j = A.col[k];
@@ -101,7 +101,7 @@ int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double e
     int32_t next = 0;
 
     std::vector<int32_t> degree(n, 0);
-    parallel_rows(n, [&](int, int64_t lo, int64_t hi) {
+    parallel_rows(n, A.nnz(), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i)
             for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) degree[i] += s[k];
     });
@@ -123,7 +123,7 @@ int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double e
 
     // pass 2 reads only the assignment after pass 1: rows are independent
     const std::vector<int32_t> after1(agg);
-    parallel_rows(n, [&](int, int64_t lo, int64_t hi) {
+    parallel_rows(n, A.nnz(), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i) {
             if (after1[i] != -1) continue;
             int32_t pick = -1;
@@ -159,6 +159,10 @@ int64_t host_aggregate(const HostCsr& A, const std::vector<double>& dg, double e
 //   aF_ik t_k over the row of A_F in column order for the k with agg(k) = j.
 // The pattern of row i is {agg(i)} union {agg(k): k in the row of A_F},
 // sorted; entries that evaluate to zero are kept.
+// Rows of at most this many nonzeros search their few coarse columns
+// linearly; longer rows (dense coarse levels) group them by sorting.
+constexpr int32_t kShortRow = 32;
+
 void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double eps,
                        const std::vector<int32_t>& agg, int64_t nagg, HostCsr& P,
                        double& omega) {
@@ -168,9 +172,9 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
     std::vector<int64_t> size(nagg, 0);
     for (int64_t i = 0; i < n; ++i) size[agg[i]]++;
     std::vector<double> t(n), dF(n);
-    const int C = row_chunks(n);
+    const int C = row_chunks(n, A.nnz());
     std::vector<double> rho_c(C, 0.0);  // per-chunk maxima; a max is order-independent
-    parallel_rows(n, [&](int c, int64_t lo, int64_t hi) {
+    parallel_rows(n, A.nnz(), [&](int c, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i) {
             t[i] = 1.0 / std::sqrt((double)size[agg[i]]);
             double weak = 0.0;
@@ -199,8 +203,9 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
     P.nrows = n;
     P.ncols = nagg;
     P.ptr.assign(n + 1, 0);
-    parallel_rows(n, [&](int c, int64_t lo, int64_t hi) {
+    parallel_rows(n, A.nnz(), [&](int c, int64_t lo, int64_t hi) {
         std::vector<std::pair<int32_t, double>> row;  // (coarse column, s_ij), few entries
+        std::vector<std::pair<int32_t, int32_t>> byc;   // long rows: (coarse column, k), stably sorted
         // thread-local output, moved into place at the end (the vector
         // objects of neighbouring chunks share cache lines)
         std::vector<int32_t> oc;
@@ -209,16 +214,46 @@ void host_prolongation(const HostCsr& A, const std::vector<double>& dg, double e
         ov.reserve(A.ptr[hi] - A.ptr[lo] + (hi - lo));
         for (int64_t i = lo; i < hi; ++i) {
             row.clear();
-            row.emplace_back(agg[i], 0.0);
-            for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-                const int32_t j = A.col[k];
-                if (j != i && !s[k]) continue;
-                const double a = (j == i) ? dF[i] : A.val[k];
-                const int32_t cc = agg[j];
-                auto it = std::find_if(row.begin(), row.end(),
-                                       [cc](const std::pair<int32_t, double>& e) { return e.first == cc; });
-                if (it == row.end()) it = row.emplace(row.end(), cc, 0.0);
-                it->second += a * t[j];
+            if (A.ptr[i + 1] - A.ptr[i] <= kShortRow) {
+                row.emplace_back(agg[i], 0.0);
+                for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                    const int32_t j = A.col[k];
+                    if (j != i && !s[k]) continue;
+                    const double a = (j == i) ? dF[i] : A.val[k];
+                    const int32_t cc = agg[j];
+                    auto it = std::find_if(row.begin(), row.end(),
+                                           [cc](const std::pair<int32_t, double>& e) { return e.first == cc; });
+                    if (it == row.end()) it = row.emplace(row.end(), cc, 0.0);
+                    it->second += a * t[j];
+                }
+            } else {
+                // long rows: group the kept entries by coarse column with a
+                // stable sort, so that each column's terms are still added in
+                // ascending k (the same sums as above, without a search per
+                // entry)
+                byc.clear();
+                for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                    const int32_t j = A.col[k];
+                    if (j != i && !s[k]) continue;
+                    byc.emplace_back(agg[j], k);
+                }
+                std::stable_sort(byc.begin(), byc.end(),
+                                 [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                                     return a.first < b.first;
+                                 });
+                bool own = false;
+                for (size_t q = 0; q < byc.size();) {
+                    const int32_t cc = byc[q].first;
+                    double sum = 0.0;
+                    for (; q < byc.size() && byc[q].first == cc; ++q) {
+                        const int32_t k = byc[q].second, j = A.col[k];
+                        const double a = (j == i) ? dF[i] : A.val[k];
+                        sum += a * t[j];
+                    }
+                    row.emplace_back(cc, sum);
+                    own = own || cc == agg[i];
+                }
+                if (!own) row.emplace_back(agg[i], 0.0);
             }
             std::sort(row.begin(), row.end());
             const double w = omega / dF[i];
@@ -255,7 +290,7 @@ void host_transpose(const HostCsr& P, HostCsr& R) {
     R.val.resize(P.nnz());
     const int64_t nc = R.nrows, n = P.nrows;
     // one chunk of rows per thread (at most 16), none for small matrices
-    const int C = row_chunks(n) == 1 ? 1 : (int)host_threads();
+    const int C = row_chunks(n, P.nnz()) == 1 ? 1 : (int)host_threads();
     if (C == 1) {
         for (int64_t k = 0; k < P.nnz(); ++k) R.ptr[P.col[k] + 1]++;
         for (int64_t c = 0; c < nc; ++c) R.ptr[c + 1] += R.ptr[c];
@@ -300,7 +335,7 @@ void host_transpose(const HostCsr& P, HostCsr& R) {
 void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const amg_params& prm,
                         std::vector<double>& d) {
     d.resize(A.nrows);
-    parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+    parallel_rows(A.nrows, A.nnz(), [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i) {
             if (prm.smoother == AMG_SMOOTHER_SPAI0) {
                 double s2 = 0.0;

@@ -185,7 +185,7 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
         AMG_CUDA(cudaMemcpyAsync(L.d, L.dhost.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         {   // values scaled by the smoother diagonal, for the fused first pre-sweep
             std::vector<double> vd(A.nnz());
-            parallel_rows(A.nrows, [&](int, int64_t lo, int64_t hi) {
+            parallel_rows(A.nrows, A.nnz(), [&](int, int64_t lo, int64_t hi) {
                 for (int64_t k = A.ptr[lo]; k < A.ptr[hi]; ++k) vd[k] = A.val[k] * L.dhost[A.col[k]];
             });
             L.A.vald = halloc<double>(h, A.nnz() + kPad);
