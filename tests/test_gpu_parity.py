@@ -193,6 +193,26 @@ def test_graph_and_host_loop_agree_bitwise(amg, torch_dev):
     assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
 
 
+def test_unaligned_solution_vector(amg, torch_dev):
+    """x at an 8-byte offset (a view into a larger tensor, odd length): the
+    solve runs on the caller's vector as it is and gives the same iterates
+    as with an aligned x."""
+    torch, dev = torch_dev
+    A = gen.poisson3d(33)
+    f, _ = gen.rhs_from_solution(A, 2)
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
+    ft = t(torch_dev, f)
+    xa = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    big = torch.zeros(A.n + 1, dtype=torch.float64, device=dev)
+    xu = big[1:]
+    assert xu.data_ptr() % 16 == 8
+    sa, ia, ra = S.solve(ft, xa, rtol=1e-8, maxiter=200)
+    su, iu, ru = S.solve(ft, xu, rtol=1e-8, maxiter=200)
+    assert sa == su == 0 and ra <= 1e-8 and ru <= 1e-8 and ia == iu
+    assert torch.equal(xa, xu)
+    S.close()
+
+
 def test_repeat_solves_deterministic_and_host_buffers(amg, torch_dev):
     A = gen.poisson3d(24)
     f, _ = gen.rhs_from_solution(A, 2)
