@@ -153,7 +153,7 @@ void launch_scale(const double* d, const double* f, double* x, int64_t n, const 
                   cudaStream_t s);
 int vec_grid(int64_t n);
 int stream_grid(int ntiles, int ctas_per_sm);  // persistent grid of the streaming engine
-constexpr int kStreamCtasMax = 3;             // most resident streaming CTAs per SM (any value type)
+constexpr int kStreamCtasMax = 4;             // most resident streaming CTAs per SM (any value type)
 void set_stream_options(bool pdl);
 int read_and_clear_dev_err();
 void enqueue_dev_err_copy(int* host_dst, cudaStream_t s);

@@ -33,7 +33,7 @@ namespace amg {
 // Persistent, warp-specialised CSR kernel.  The matrix is split into tiles
 // (consecutive rows, at most kTileNnz nonzeros and kRowsPerBlock rows); CTA b
 // owns a contiguous run of tiles.  One producer lane streams each tile's row
-// pointers, column indices and values into a kStages-deep shared-memory ring
+// pointers, column indices and values into a shared-memory ring of stages
 // with bulk asynchronous copies (cp.async.bulk, completion counted on an
 // mbarrier, evict-first in L2 so that the gathered vectors stay resident);
 // eight consumer warps take `vw` lanes per row, gather the operand through
@@ -42,12 +42,15 @@ namespace amg {
 // data -- before waiting for the previous kernel, so consecutive kernels of
 // the solve overlap their pipeline fill with the predecessor's tail.
 constexpr int kCons = kConsumers;
-constexpr int kStages = 3;
 
-// Resident CTAs per SM: the shared-memory ring of a float64 kernel
-// (3 stages of about 26 KB) allows two, that of a float32 or bfloat16 kernel
-// (about 24 KB or less per stage) three.  More tiles in flight per SM hide
-// more of the gather latency.
+// Ring depth and resident CTAs per SM.  A float64 kernel keeps 3 stages of
+// about 34 KB and two CTAs per SM; the float32 and bfloat16 kernels, bound by
+// gather latency rather than by a pipe, trade depth for CTAs: 2 stages of at
+// most about 24 KB and four CTAs per SM (their registers then fit 56 per
+// thread).  More tiles in flight per SM hide more of the gather latency;
+// measured on the 150^3 V-cycles, four CTAs of 2 stages beat three of 3.
+template <typename VT>
+__host__ __device__ constexpr int stages() { return sizeof(VT) >= 8 ? 3 : 2; }
 template <typename VT>
 __host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 2 : kStreamCtasMax; }
 
@@ -90,7 +93,7 @@ struct StreamLayout {
     }
     static constexpr size_t stage = rp_bytes + col_bytes + val_bytes + vec_off(NV);
     static constexpr size_t header = 128;
-    static constexpr size_t total = header + kStages * stage;
+    static constexpr size_t total = header + stages<VT>() * stage;
     static_assert(rp_bytes % 16 == 0 && col_bytes % 16 == 0 && val_bytes % 16 == 0 && stage % 16 == 0,
                   "bulk-copy destinations must stay 16-byte aligned");
 };
@@ -151,7 +154,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-constexpr int kGatherBatch = 8;
+constexpr int kGatherBatch = 4;
 
 // sum -/+ the products of nonzeros k, k + vw, ... < ke, in that order; the
 // columns, values and gathered operands of kGatherBatch nonzeros at a time
@@ -189,6 +192,7 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     using acc_t = typename Epi::acc_t;
     constexpr int NV = Epi::nvec;
     using L = StreamLayout<VT, RMAX, Epi>;
+    constexpr int kStages = stages<VT>();  // at most 3: the 128-byte header holds their barriers
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* empty = full + kStages;
