@@ -339,6 +339,18 @@ amg_status amg_solve_profile(amg_handle *h, const double *f, double *x, double r
  * loop iterations included). */
 amg_status amg_last_launch_count(const amg_handle *h, int64_t *launches);
 
+/* Check of failure detection (no counterpart in the paper): on the current
+ * device, one block of the streaming engine's pipeline waits on a barrier
+ * that nothing completes, with the engine's bounded wait limited to 2^12 polls
+ * (at most about 0.4 s).  The wait gives up, records the timeout in the
+ * device error word and returns, as a streaming kernel whose copies never
+ * arrived would.  The call reads and clears that word and returns
+ * AMG_ERR_CUDA with the message a solve gives for it; *seconds (may be NULL)
+ * receives the kernel's duration.  The device stays usable.  The error word
+ * is shared by all handles of the process: do not run this while solves are
+ * in flight. */
+amg_status amg_check_wait_limit(double *seconds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ _sigs = {
     "amg_spmv_dot_noalloc": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
+    "amg_check_wait_limit": [C.POINTER(_D)],
     "amg_batch_setup": [_I, _VP, C.POINTER(amg_params), _VP, C.POINTER(_VP)],
     "amg_batch_solve": [_VP, _VP, _VP, _D, _I, _VP, _VP, _VP],
     "amg_batch_tune": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_I)],
@@ -196,6 +197,14 @@ def amg_solve_profile(h, f, x, rtol=1e-8, maxiter=500):
     _check(st, "amg_solve_profile", (AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN))
     return (st, it.value, rr.value, dict(zip(KERNEL_CLASSES, list(ms))),
             dict(zip(KERNEL_CLASSES, list(ln))))
+
+
+def amg_check_wait_limit():
+    """Run the bounded-wait check (see include/amg.h); returns (status, seconds).
+    The expected status is AMG_ERR_CUDA."""
+    sec = C.c_double()
+    st = _lib.amg_check_wait_limit(C.byref(sec))
+    return st, sec.value
 
 
 def amg_last_launch_count(h) -> int:

@@ -230,6 +230,9 @@ struct TailPlan {
 };
 void launch_tail(const TailPlan& plan, bool f32, const int* skip, cudaStream_t s);
 int* dev_err_ptr();
+// Runs the bounded-wait check kernel on the current device; returns the device
+// error word it left (cleared afterwards) and the kernel's duration.
+int check_wait_limit(double* seconds);
 
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.

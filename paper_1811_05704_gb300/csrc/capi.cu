@@ -347,6 +347,14 @@ amg_status amg_solve_profile(amg_handle* h, const double* f, double* x, double r
     });
 }
 
+amg_status amg_check_wait_limit(double* seconds) {
+    return guarded([&]() -> amg_status {
+        const int err = check_wait_limit(seconds);
+        if (err & 4) fail(AMG_ERR_CUDA, "a device pipeline wait timed out (bounded-wait check)");
+        fail(AMG_ERR_CUDA, "the bounded-wait check kernel did not record its timeout");
+    });
+}
+
 amg_status amg_last_launch_count(const amg_handle* h, int64_t* launches) {
     if (!h || !launches) return AMG_ERR_INVALID_ARG;
     *launches = h->last_launches;

@@ -121,15 +121,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: each poll suspends for at most 100 us, and after 2^15 polls
-// (at most about 3.3 s) the wait gives up, records bit 2 in g_dev_err and
-// returns false instead of spinning forever.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 15); ++i)
+// Bounded wait: each poll suspends for at most 100 us, and after kPolls polls
+// (2^15 in the kernels: at most about 3.3 s) the wait gives up, records bit 2
+// in g_dev_err and returns false instead of spinning forever.
+template <uint32_t kPolls>
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* b, uint32_t parity) {
+    for (uint32_t i = 0; i < kPolls; ++i)
         if (mbar_try(b, parity)) return true;
     atomicOr(&g_dev_err, 4);
     return false;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) { return mbar_wait_n<1u << 15>(b, parity); }
 __device__ __forceinline__ uint64_t evict_first_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -504,6 +506,35 @@ int stream_grid(int ntiles, int ctas_per_sm) {
         g_sm_count.store(sms);
     }
     return std::max(1, std::min(ntiles, ctas_per_sm * sms));
+}
+
+// Check of the bounded wait: one block waits on a pipeline barrier that no
+// copy or thread ever completes, with the streaming kernels' wait limited to
+// 2^12 polls (at most about 0.4 s).  Every thread gives up, bit 2 of the
+// device error word is set, and the kernel returns.
+__global__ void k_wait_unfilled() {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    mbar_wait_n<1u << 12>(&bar, 0);
+}
+
+int check_wait_limit(double* seconds) {
+    read_and_clear_dev_err();  // start from a clear error word
+    cudaEvent_t e0, e1;
+    AMG_CUDA(cudaEventCreate(&e0));
+    AMG_CUDA(cudaEventCreate(&e1));
+    AMG_CUDA(cudaEventRecord(e0, 0));
+    k_wait_unfilled<<<1, 32>>>();
+    AMG_CUDA(cudaGetLastError());
+    AMG_CUDA(cudaEventRecord(e1, 0));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    AMG_CUDA(cudaEventDestroy(e0));
+    AMG_CUDA(cudaEventDestroy(e1));
+    if (seconds) *seconds = ms * 1e-3;
+    return read_and_clear_dev_err();
 }
 
 int* dev_err_ptr() {
