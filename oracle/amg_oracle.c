@@ -26,7 +26,10 @@
  *
  * Pins: every function here is checked in tests/test_oracle_pins.py against
  * closed forms, invariants, dense linear algebra (numpy) on tiny inputs or
- * hand-derived values; none is "parity unpinned".
+ * hand-derived values.  The per-level strength schedule of the setup
+ * (eps_l = eps_0 0.5^l) is pinned by comparing each level's aggregates with a
+ * standalone aggregation of that level's matrix at eps_l, on a problem where
+ * eps_l / 2 and 2 eps_l aggregate differently.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * integer decisions that depend on floating point -- strength of connection,

@@ -376,6 +376,49 @@ def test_spgemm_standalone_matches_dense(oracle_lib):
         assert np.all(np.diff(col[ptr[i]:ptr[i + 1]]) > 0)
 
 
+def _level_csr(H, l):
+    ptr, col, val, shape = H.matrix(l, "A")
+    return Csr(shape[0], ptr.astype(np.int32), col, val)
+
+
+def test_strength_schedule_halves_per_level(oracle_lib):
+    """The strength threshold of level l is eps_0 * 0.5^l (the schedule of the
+    smoothed aggregation that Sec. 3 cites, Vanek, Mandel and Brezina 1996),
+    and a constant eps_0 with the halving switched off.  Each level's
+    aggregates inside the hierarchy must equal the standalone aggregation of
+    that level's matrix at the scheduled threshold.  The problem is chosen so
+    that on levels 1 and 2 the thresholds eps/2, eps and 2 eps give three
+    different aggregations: skipping the halving, applying it twice per level
+    or starting it one level early each fails."""
+    A = gen.varcoef3d(10, seed=0)
+    H = _hier(A, coarse_enough=20)
+    assert H.levels >= 4
+    for l in (1, 2, 3):
+        eps = 0.08 * 0.5 ** l
+        Al = _level_csr(H, l)
+        got = H.aggregates(l)
+        want, nagg = oracle_lib.aggregate(Al, eps)
+        assert np.array_equal(got, want), l
+        assert H.level_info(l + 1)["n"] == nagg
+        if l < 3:
+            for wrong in (2 * eps, 0.5 * eps):
+                assert not np.array_equal(got, oracle_lib.aggregate(Al, wrong)[0]), (l, wrong)
+    # the finest level always uses eps_0
+    assert np.array_equal(H.aggregates(0), oracle_lib.aggregate(A, 0.08)[0])
+    # constant threshold with the halving off: level 1 aggregates at eps_0;
+    # level 2 then keeps more than 95% of its rows at eps_0 (the stall rule
+    # makes it the coarsest), where the halved threshold would coarsen on
+    H0 = _hier(A, coarse_enough=20, eps_halving=0)
+    A1 = _level_csr(H0, 1)
+    got = H0.aggregates(1)
+    assert np.array_equal(got, oracle_lib.aggregate(A1, 0.08)[0])
+    assert not np.array_equal(got, oracle_lib.aggregate(A1, 0.04)[0])
+    A2 = _level_csr(H0, 2)
+    assert H0.levels == 3
+    assert oracle_lib.aggregate(A2, 0.08)[1] >= 0.95 * A2.n
+    assert oracle_lib.aggregate(A2, 0.04)[1] < 0.95 * A2.n
+
+
 def test_coarse_levels_symmetric(oracle_lib):
     H = _hier(gen.varcoef3d(12, seed=2), coarse_enough=30)
     assert H.levels >= 3
