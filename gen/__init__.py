@@ -18,6 +18,7 @@ from .problems import (
     convdiff3d,
     rhs_from_solution,
     uniform_pm1,
+    sample_indices,
     poisson3d_nnz,
     batched_sides,
     serving_sides,
@@ -36,6 +37,7 @@ __all__ = [
     "convdiff3d",
     "rhs_from_solution",
     "uniform_pm1",
+    "sample_indices",
     "poisson3d_nnz",
     "batched_sides",
     "serving_sides",

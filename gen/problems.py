@@ -29,6 +29,7 @@ STREAM_KIND = 20
 STREAM_REUSE = 21
 STREAM_PICK = 22
 STREAM_ARRIVAL = 23
+STREAM_SAMPLE = 30
 STREAM_REQ_RHS = 100000  # + request index
 SERVE_VARCOEF_RANGE = (-2.0, 2.0)  # log10 of the cell coefficients of served SPD requests
 
@@ -219,6 +220,13 @@ def rhs_from_solution(A: Csr, seed: int):
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
     f = np.bincount(rows, weights=A.val * ustar[A.col], minlength=A.n)
     return f, ustar
+
+
+def sample_indices(n: int, count: int, seed: int) -> np.ndarray:
+    """Up to `count` distinct indices in [0, n), sorted, drawn uniformly from the
+    seeded stream (which entries of a large vector a test compares)."""
+    u = uniform01(seed, STREAM_SAMPLE, count)
+    return np.unique(np.minimum((u * n).astype(np.int64), n - 1))
 
 
 def batched_sides(count: int, seed: int, lo: int = 16, hi: int = 128):

@@ -339,6 +339,17 @@ amg_status amg_solve_profile(amg_handle *h, const double *f, double *x, double r
  * loop iterations included). */
 amg_status amg_last_launch_count(const amg_handle *h, int64_t *launches);
 
+/* How the last amg_solve / amg_solve_host on this handle ran (Sec. 3: the
+ * solve phase; no counterpart for the launch mode itself).  A solve is one or
+ * more attempts: the first run of the Krylov loop, plus one per restart from
+ * the true residual.  *graph_attempts (may be NULL) receives the number of
+ * attempts launched as one CUDA graph with a device-side loop;
+ * *host_attempts (may be NULL) the number whose kernels were launched one by
+ * one from the host, because use_graph = 0 or because the graph could not be
+ * built (the handle then keeps to host launches).  Both are 0 before the
+ * first solve. */
+amg_status amg_last_solve_mode(const amg_handle *h, int *graph_attempts, int *host_attempts);
+
 /* Check of failure detection (no counterpart in the paper): on the current
  * device, one block of the streaming engine's pipeline waits on a barrier
  * that nothing completes, with the engine's bounded wait limited to 2^12 polls

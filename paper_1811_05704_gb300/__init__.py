@@ -82,6 +82,7 @@ _sigs = {
     "amg_spmv_dot_noalloc": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
+    "amg_last_solve_mode": [_VP, C.POINTER(_I), C.POINTER(_I)],
     "amg_check_wait_limit": [C.POINTER(_D)],
     "amg_batch_setup": [_I, _VP, C.POINTER(amg_params), _VP, C.POINTER(_VP)],
     "amg_batch_solve": [_VP, _VP, _VP, _D, _I, _VP, _VP, _VP],
@@ -211,6 +212,13 @@ def amg_last_launch_count(h) -> int:
     v = C.c_int64()
     _check(_lib.amg_last_launch_count(h, C.byref(v)), "amg_last_launch_count")
     return v.value
+
+
+def amg_last_solve_mode(h):
+    """(graph attempts, host-launched attempts) of the last solve."""
+    g, hst = C.c_int(), C.c_int()
+    _check(_lib.amg_last_solve_mode(h, C.byref(g), C.byref(hst)), "amg_last_solve_mode")
+    return g.value, hst.value
 
 
 def amg_hierarchy_info(h):

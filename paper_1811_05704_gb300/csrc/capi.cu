@@ -361,6 +361,13 @@ amg_status amg_last_launch_count(const amg_handle* h, int64_t* launches) {
     return AMG_OK;
 }
 
+amg_status amg_last_solve_mode(const amg_handle* h, int* graph_attempts, int* host_attempts) {
+    if (!h) return AMG_ERR_INVALID_ARG;
+    if (graph_attempts) *graph_attempts = h->last_graph_attempts;
+    if (host_attempts) *host_attempts = h->last_host_attempts;
+    return AMG_OK;
+}
+
 amg_status amg_hierarchy_info(const amg_handle* h, int* levels, int64_t* rows, int64_t* nnz_a,
                               int64_t* nnz_p) {
     return guarded([&]() -> amg_status {

@@ -80,5 +80,8 @@ struct amg_handle {
     std::vector<amg::CachedGraph> graphs;
     bool graph_unsupported = false;
     int64_t last_launches = 0;
+    // attempts of the last solve (first run and restarts) launched as one
+    // graph, and launched kernel by kernel from the host
+    int last_graph_attempts = 0, last_host_attempts = 0;
     std::vector<cudaEvent_t> event_pool;
 };

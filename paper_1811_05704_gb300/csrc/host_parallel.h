@@ -57,6 +57,63 @@ void parallel_for(int64_t n, F&& fn) {
     if (err) std::rethrow_exception(err);
 }
 
+// fn(s, t, T) for steps s = 0 .. nsteps-1 on a team of T threads (t = 0 ..
+// T-1); a step starts on every thread only after every thread finished the
+// previous one (a spinning barrier), and before(s) runs on thread 0 alone
+// between step s-1 and step s.  The team is created once, so many short steps
+// (the pivot steps of a dense factorisation) do not pay a thread start each.
+template <class B, class F>
+void parallel_steps(int64_t nsteps, B&& before, F&& fn) {
+    const unsigned T = host_threads();
+    std::atomic<unsigned> arrived{0};
+    std::atomic<int64_t> started{0};  // steps whose before() ran (monotone)
+    std::atomic<int64_t> done{0};     // steps every thread finished (monotone)
+    std::atomic<bool> failed{false};
+    std::exception_ptr err;
+    std::mutex m;
+    auto record = [&]() {
+        std::lock_guard<std::mutex> g(m);
+        if (!err) err = std::current_exception();
+        failed.store(true);
+    };
+    auto body = [&](unsigned t) {
+        for (int64_t s = 0; s < nsteps; ++s) {
+            if (t == 0) {
+                if (!failed.load()) {
+                    try {
+                        before(s);
+                    } catch (...) {
+                        record();
+                    }
+                }
+                started.store(s + 1, std::memory_order_release);
+            } else {
+                while (started.load(std::memory_order_acquire) < s + 1) std::this_thread::yield();
+            }
+            if (!failed.load()) {
+                try {
+                    fn(s, t, T);
+                } catch (...) {
+                    record();
+                }
+            }
+            // barrier: the last thread to arrive resets the count, then
+            // publishes the step as done
+            if (arrived.fetch_add(1, std::memory_order_acq_rel) + 1 == T) {
+                arrived.store(0, std::memory_order_relaxed);
+                done.store(s + 1, std::memory_order_release);
+            } else {
+                while (done.load(std::memory_order_acquire) < s + 1) std::this_thread::yield();
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < T; ++t) pool.emplace_back(body, t);
+    body(0);
+    for (auto& th : pool) th.join();
+    if (err) std::rethrow_exception(err);
+}
+
 // Number of chunks for n rows holding `work` nonzeros: one per 65,536 rows
 // or per 262,144 nonzeros, whichever gives more (coarse levels have few rows
 // of many nonzeros), at most 64 and at most n; small matrices (and the many

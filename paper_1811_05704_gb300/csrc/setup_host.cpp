@@ -350,7 +350,11 @@ void host_smoother_diag(const HostCsr& A, const std::vector<double>& dg, const a
 
 // Coarsest direct solver (Algorithm 1, last step): LU with partial pivoting
 // (largest magnitude, lowest row on ties), then the explicit inverse, so that
-// the solve on the GPU is one matrix-vector product.
+// the solve on the GPU is one matrix-vector product.  Large matrices run on
+// a team of host threads: the rows below a pivot are updated in parallel
+// (each entry still receives its updates in pivot order), and the columns of
+// the inverse are independent solves; the result does not depend on the
+// thread count.
 void host_dense_inverse(const HostCsr& A, std::vector<double>& inv) {
     const int64_t n = A.nrows;
     std::vector<double> a(n * n, 0.0);
@@ -358,7 +362,7 @@ void host_dense_inverse(const HostCsr& A, std::vector<double>& inv) {
         for (int32_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) a[i * n + A.col[k]] = A.val[k];
     std::vector<int64_t> perm(n);
     for (int64_t i = 0; i < n; ++i) perm[i] = i;
-    for (int64_t c = 0; c < n; ++c) {
+    auto pivot = [&](int64_t c) {
         int64_t p = c;
         for (int64_t i = c + 1; i < n; ++i)
             if (std::fabs(a[i * n + c]) > std::fabs(a[p * n + c])) p = i;
@@ -367,17 +371,27 @@ void host_dense_inverse(const HostCsr& A, std::vector<double>& inv) {
             std::swap_ranges(a.begin() + c * n, a.begin() + c * n + n, a.begin() + p * n);
             std::swap(perm[c], perm[p]);
         }
-        const double piv = a[c * n + c];
-        for (int64_t i = c + 1; i < n; ++i) {
-            const double l = a[i * n + c] / piv;
-            a[i * n + c] = l;
-            if (l != 0.0)
-                for (int64_t j = c + 1; j < n; ++j) a[i * n + j] -= l * a[c * n + j];
+    };
+    auto eliminate = [&](int64_t c, int64_t i) {
+        const double l = a[i * n + c] / a[c * n + c];
+        a[i * n + c] = l;
+        if (l != 0.0)
+            for (int64_t j = c + 1; j < n; ++j) a[i * n + j] -= l * a[c * n + j];
+    };
+    const bool team = n >= 256 && host_threads() > 1;
+    if (team) {
+        parallel_steps(n, pivot, [&](int64_t c, unsigned t, unsigned T) {
+            for (int64_t i = c + 1 + t; i < n; i += T) eliminate(c, i);
+        });
+    } else {
+        for (int64_t c = 0; c < n; ++c) {
+            pivot(c);
+            for (int64_t i = c + 1; i < n; ++i) eliminate(c, i);
         }
     }
     inv.assign(n * n, 0.0);
-    std::vector<double> y(n);
-    for (int64_t e = 0; e < n; ++e) {  // column e of A^{-1}: solve A x = e_e
+    // column e of A^{-1}: solve A x = e_e with the factors
+    auto column = [&](int64_t e, std::vector<double>& y) {
         for (int64_t i = 0; i < n; ++i) {
             double v = (perm[i] == e) ? 1.0 : 0.0;
             for (int64_t j = 0; j < i; ++j) v -= a[i * n + j] * y[j];
@@ -389,6 +403,16 @@ void host_dense_inverse(const HostCsr& A, std::vector<double>& inv) {
             y[i] = v / a[i * n + i];
         }
         for (int64_t i = 0; i < n; ++i) inv[i * n + e] = y[i];
+    };
+    if (team) {
+        const int64_t C = std::min<int64_t>(n, 64);
+        parallel_for(C, [&](int64_t c) {
+            std::vector<double> y(n);
+            for (int64_t e = n * c / C; e < n * (c + 1) / C; ++e) column(e, y);
+        });
+    } else {
+        std::vector<double> y(n);
+        for (int64_t e = 0; e < n; ++e) column(e, y);
     }
 }
 

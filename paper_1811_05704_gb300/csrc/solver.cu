@@ -632,6 +632,7 @@ static int64_t attempt(amg_handle* h, const double* f, double* x, bool use_graph
         }
         CachedGraph& g = *gp;
         const int it0 = h->st_in->it;
+        ++h->last_graph_attempts;
         AMG_CUDA(cudaGraphLaunch(g.exec, h->stream));
         AMG_CUDA(cudaStreamSynchronize(h->stream));
         const int64_t iters = std::max(0, h->st_out->it - it0);
@@ -640,6 +641,7 @@ static int64_t attempt(amg_handle* h, const double* f, double* x, bool use_graph
     Issue local;
     Issue& I = prof ? *prof : local;
     I.s = h->stream;
+    ++h->last_host_attempts;
     const int64_t l0 = I.launches;
     Reduce b = base_reduce(h);
     AMG_CUDA(cudaMemcpyAsync(h->st, h->st_in, sizeof(KState), cudaMemcpyHostToDevice, h->stream));
@@ -669,6 +671,7 @@ amg_status run_solve(amg_handle* h, const double* f, double* x, double rtol, int
     h->st_in->maxiter = maxiter;
     bool use_graph = h->prm.use_graph && !h->graph_unsupported && !prof;
     int64_t launches = 0;
+    h->last_graph_attempts = h->last_host_attempts = 0;
     amg_status status = AMG_OK;
     for (int attempt_no = 0; attempt_no < 64; ++attempt_no) {
         *h->err_host = 0;
