@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-serial-sample", type=int, default=200,
+                    help="requests of the plain-API baseline (evenly spaced, scaled to the stream); 0 = all")
+    ap.add_argument("--no-varcoef", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
@@ -365,8 +368,10 @@ def bench_batched(amg, torch, dev, stream, args, rank=0, world=1):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
         assert st == 0 and (rr <= RTOL).all()
+    iter_bytes = amg.amg_batch_bytes(b, nsys)
     amg.amg_batch_free(b)
     batch_s = max_over_ranks(statistics.median(times), world, dev)
+    moved = float(sum(gather_lists([float(np.dot(iter_bytes, it))], world)))
     # plain FP64 path: one handle and one solve per system, on a sample
     sample = list(range(0, nsys, max(1, nsys // 128)))
     plain = 0.0
@@ -391,10 +396,63 @@ def bench_batched(amg, torch, dev, stream, args, rank=0, world=1):
             "iterations_mean": float(np.mean(it)), "iterations_max": int(np.max(it)),
             "levels_max": int(max_over_ranks(lev.max(), world, dev)),
             "schedule": {"threads": threads, "ctas_per_sm": ctas},
+            "hbm_gbs": moved / batch_s / 1e9,
+            "frac_of_peak": moved / batch_s / 1e9 / peaks()[0],
+            "bytes_note": "algorithmic bytes (amg_batch_bytes: each system's bytes per CG iteration, float32 "
+                          "V-cycle model) x its iterations, summed over the systems, / the batch solve time",
             "plain_fp64_solve_s": plain_s,
             "plain_note": f"amg_solve per system (FP64, CUDA graph) on {len(sample)} evenly spaced systems"
                           f" of each rank's {nsys}, scaled to them (slowest rank)",
             "speedup_vs_plain": plain_s / batch_s}
+
+
+def bench_varcoef(amg, torch, dev, stream, args, rank=0, world=1):
+    """The 200^3 variable-coefficient workload (8,000,000 unknowns, 55,760,000
+    nonzeros; k = 10^U(-3,3) per cell, 10% of the cells with z-anisotropy 0.01,
+    harmonic-mean faces; f = A u*, x0 = 0), rtol 1e-8: set-up time, then the
+    FP64 solve and the FP32 and bfloat16-stored V-cycles under FP64 CG, each
+    timed with CUDA events over `reps` solves on the resident hierarchy, with
+    algorithmic GB/s (amg_hierarchy_bytes x iterations / solve time).  With
+    several ranks every rank solves the whole problem (replicas)."""
+    A = gen.varcoef3d(200, seed=0)
+    f, _ = gen.rhs_from_solution(A, 0)
+    ft = torch.from_numpy(f).to(dev)
+    x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    reps = 3
+    out = {"workload": "varcoef3d-200^3 FV diffusion, k = 10^U(-3,3), 10% z-anisotropy 0.01, f = A u*, rtol 1e-8",
+           "unknowns": A.n, "nnz": A.nnz, "reps": reps}
+    x64 = None
+    peak = peaks()[0]
+    for name, prec in (("fp64", amg.AMG_PRECISION_FP64), ("fp32", amg.AMG_PRECISION_FP32),
+                       ("bf16", amg.AMG_PRECISION_BF16)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=prec)
+        setup_s = time.perf_counter() - t0
+        info = S.info()
+        x.zero_()
+        S.solve(ft, x, RTOL, 500)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            x.zero_()
+            st, it, rr = S.solve(ft, x, RTOL, 500)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solve_s = max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps, world, dev)
+        gbs = amg.amg_hierarchy_bytes(S.handle) * it / solve_s / 1e9
+        r = {"setup_s": max_over_ranks(setup_s, world, dev), "solve_s": solve_s, "iterations": it, "relres": rr,
+             "status": st, "hbm_gbs": gbs, "frac_of_peak": gbs / peak, "levels": info["levels"],
+             "operator_complexity": sum(info["nnz"]) / info["nnz"][0]}
+        if x64 is None:
+            x64 = x.clone()
+        else:
+            r["rel_diff_vs_fp64_x"] = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+            r["speedup_vs_fp64"] = out["fp64"]["solve_s"] / solve_s
+        out[name] = r
+        S.close()
+    return out
 
 
 def _serve_matrices(reqs):
@@ -446,17 +504,21 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
     last_use = {q.key: q.index for q in reqs}
     rows = sum(gather_lists([int(sum(A_of(q).n for q in reqs))], world))
 
-    # plain API, one request after another
+    # plain API, one request after another: on every `stride`-th request of
+    # this rank's stream (all of them for short streams), scaled to the stream
+    stride = max(1, len(reqs) // args.serve_serial_sample) if args.serve_serial_sample > 0 else 1
+    sample = reqs[::stride]
+    last_in_sample = {q.key: q.index for q in sample}
     handles, serial_status = {}, {}
     t0 = time.perf_counter()
-    for q in reqs:
+    for q in sample:
         if q.key not in handles:
             handles[q.key] = amg.amg_setup(csrs[(q.kind, q.side)], prm_of(q))
         x = np.zeros(A_of(q).n)
         serial_status[q.index] = amg.amg_solve_host(handles[q.key], rhs[q.index], x, RTOL, MAXITER)[0]
-        if last_use[q.key] == q.index:
+        if last_in_sample[q.key] == q.index:
             amg.amg_free(handles.pop(q.key))
-    serial_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    serial_s = max_over_ranks((time.perf_counter() - t0) * len(reqs) / max(1, len(sample)), world, dev)
 
     def run(arrival):
         """Submit every request at its arrival time (None: all at once),
@@ -474,6 +536,7 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
         res = [amg.amg_server_wait(srv, rid, A_of(q).n) for q, rid in zip(reqs, ids)]
         wall = time.perf_counter() - t_start
         stats = amg.amg_server_stats(srv)
+        stats["solve_bytes"] = amg.amg_server_solve_bytes(srv)
         amg.amg_server_destroy(srv)
         return wall, res, stats
 
@@ -486,12 +549,13 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
     open_s, open_res, open_stats = run(unit_arrivals / rate)
     open_s = max_over_ranks(open_s, world, dev)
     lat = np.array(gather_lists([float(r[4]) for r in open_res], world)) * 1e3
+    moved = float(sum(gather_lists([float(sat_stats["solve_bytes"])], world)))
     ok = all(r[0] == 0 and r[3] <= RTOL for r in sat_res + open_res) and all(s == 0 for s in serial_status.values())
     ok = all(gather_lists([ok], world))
     failed = [{"index": q.index, "kind": q.kind, "side": q.side, "status": [r[0], o[0], serial_status[q.index]],
                "iters": r[2], "relres": r[3]}
               for q, r, o in zip(reqs, sat_res, open_res)
-              if r[0] != 0 or o[0] != 0 or serial_status[q.index] != 0 or r[3] > RTOL][:10]
+              if r[0] != 0 or o[0] != 0 or serial_status.get(q.index, 0) != 0 or r[3] > RTOL][:10]
     failed = gather_lists(failed, world)[:10]
     same = all(gather_lists([all(np.array_equal(a[1], b[1]) for a, b in zip(sat_res, open_res))], world))
     return {"workload": f"{nreq} requests, sides log-uniform [20,160], 70% SPD (CG) / 30% convdiff (BiCGStab), "
@@ -501,6 +565,14 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
             "same_result_saturated_and_open_loop": same,
             "value": sat_rate, "unit": "requests/s (setup + solve)", "saturated_s": sat_s,
             "serial_plain_s": serial_s, "serial_plain_rate": nreq / serial_s, "speedup_vs_serial": serial_s / sat_s,
+            "serial_note": (f"plain API (amg_setup + amg_solve_host, a hierarchy kept until its key's last sampled "
+                            f"request) on every {stride}-th request ({len(sample)} of {len(reqs)} per rank), "
+                            "time scaled to the whole stream") if stride > 1 else
+                           "plain API on every request (amg_setup + amg_solve_host)",
+            "solve_hbm_gbs": moved / sat_s / 1e9,
+            "solve_frac_of_peak": moved / sat_s / 1e9 / peaks()[0],
+            "bytes_note": "algorithmic bytes of the served solves (amg_server_solve_bytes: each solve's bytes per "
+                          "Krylov iteration x its iterations) / the saturated wall time, set-ups included in the time",
             "open_loop_rate": rate, "open_loop_s": open_s,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
@@ -579,6 +651,7 @@ def main():
     value = world * args.steps / total_s
     solve_s = statistics.median(step_ms) / 1e3
     b_iter = bytes_per_iteration(info, coarse_n)
+    assert abs(b_iter - amg.amg_hierarchy_bytes(S.handle)) <= 1e-9 * b_iter, "byte models disagree"
     solve_gbs = b_iter * iters[0] / solve_s / 1e9
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -665,6 +738,10 @@ def main():
                                         "algorithmic_bytes_per_launch": kbm[mdom], "avg_launch_ms": mavg}}
             S32.close()
 
+    varcoef = None
+    if not args.no_varcoef:
+        varcoef = bench_varcoef(amg, torch, dev, stream, args, rank, world)
+
     batched = None
     if not args.no_batch:
         batched = bench_batched(amg, torch, dev, stream, args, rank, world)
@@ -704,6 +781,7 @@ def main():
         "solve_frac_of_nominal": solve_gbs / NOMINAL_HBM_GBS,
         "kernels": per_kernel,
         "mixed": mixed,
+        "varcoef200": varcoef,
         "batched": batched,
         "serving": serving,
         "clocks": clock_info,

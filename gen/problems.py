@@ -132,6 +132,51 @@ def poisson2d_shift(m: int, sigma: float) -> Csr:
     return _assemble(n, offs, cols, vals, masks)
 
 
+# Transcendental functions of numpy and libm may round differently on
+# different machines (vectorised implementations, contracted multiply-adds),
+# which would make the same seed give different matrices on the x86 build host
+# and the Arm GPU host.  The generators therefore use only +, -, *, / and
+# sqrt, which IEEE 754 rounds the same everywhere.
+_LN10 = 2.302585092994046       # ln 10
+_LN2 = 0.6931471805599453        # ln 2
+
+
+def _exp_small(y: np.ndarray) -> np.ndarray:
+    """exp(y) for 0 <= y < 2.5, from basic operations only: exp(y / 32) by a
+    degree-12 Taylor polynomial (Horner; truncation error below 1e-22
+    relative), squared five times."""
+    z = np.asarray(y, dtype=np.float64) / 32.0
+    p = np.ones_like(z)
+    for k in range(12, 0, -1):
+        p = 1.0 + p * z / k
+    for _ in range(5):
+        p = p * p
+    return p
+
+
+def _ln_det(x: float) -> float:
+    """ln(x) for x > 0 from basic operations: x = 2^e m with m in [1, 2)
+    (exact), ln m = 2 atanh((m - 1)/(m + 1)) by its series (|y| <= 1/3,
+    30 terms)."""
+    m, e = np.frexp(np.float64(x))  # x = m 2^e, m in [0.5, 1)
+    m, e = m * 2.0, e - 1
+    y = (m - 1.0) / (m + 1.0)
+    y2 = y * y
+    acc = 0.0
+    for k in range(29, -1, -1):
+        acc = 1.0 / (2 * k + 1) + y2 * acc
+    return float(e * _LN2 + 2.0 * y * acc)
+
+
+def exp10_det(x: np.ndarray) -> np.ndarray:
+    """10^x for x in [-3, 3], the same bits on every machine: 10^floor(x)
+    (a table of the double constants 1e-3 .. 1e3) times exp(frac(x) ln 10)."""
+    x = np.asarray(x, dtype=np.float64)
+    e = np.floor(x)
+    table = np.array([1e-3, 1e-2, 1e-1, 1.0, 1e1, 1e2, 1e3])
+    return table[(e + 3).astype(np.int64)] * _exp_small((x - e) * _LN10)
+
+
 def varcoef3d(m: int, seed: int, log10_range=(-3.0, 3.0), aniso_frac=0.1, aniso_z=0.01) -> Csr:
     """Cell-centred finite-volume diffusion with per-cell coefficient.
 
@@ -145,7 +190,9 @@ def varcoef3d(m: int, seed: int, log10_range=(-3.0, 3.0), aniso_frac=0.1, aniso_
     n = m ** 3
     idx, i, j, k = _grid3(m)
     lo, hi = log10_range
-    kc = 10.0 ** (lo + (hi - lo) * uniform01(seed, STREAM_COEF, n))
+    if not (-3.0 <= lo <= hi <= 3.0):
+        raise ValueError("log10_range must lie within [-3, 3]")
+    kc = exp10_det(lo + (hi - lo) * uniform01(seed, STREAM_COEF, n))
     aniso = uniform01(seed, STREAM_ANISO, n) < aniso_frac
     kd = [kc, kc, np.where(aniso, aniso_z * kc, kc)]  # x, y, z coefficients
 
@@ -179,7 +226,9 @@ def varcoef3d(m: int, seed: int, log10_range=(-3.0, 3.0), aniso_frac=0.1, aniso_
 def convdiff3d(m: int, seed: int, pe_range=(1.0, 100.0)):
     """Upwind convection-diffusion: 7-point diffusion plus first-order upwinding.
 
-    Velocity v is a seeded unit vector (uniform on the sphere), the cell Peclet
+    Velocity v is a seeded unit vector (uniform on the sphere, by Marsaglia's
+    rejection method: (x1, x2) uniform in the unit disc, v = (2 x1 sqrt(1-s),
+    2 x2 sqrt(1-s), 1 - 2 s) with s = x1^2 + x2^2), the cell Peclet
     number Pe ~ U(pe_range).  For each axis d with c_d = Pe*|v_d|, c_d is added
     to the diagonal and -c_d to the coefficient of the upwind neighbour (the one
     at -sign(v_d)); an upwind neighbour outside the grid is eliminated like the
@@ -188,12 +237,15 @@ def convdiff3d(m: int, seed: int, pe_range=(1.0, 100.0)):
     """
     n = m ** 3
     idx, i, j, k = _grid3(m)
-    u = uniform01(seed, STREAM_VEL, 3)
-    z = 2.0 * u[0] - 1.0
-    phi = 2.0 * np.pi * u[1]
-    r = np.sqrt(max(0.0, 1.0 - z * z))
-    v = np.array([r * np.cos(phi), r * np.sin(phi), z])
-    pe = pe_range[0] + (pe_range[1] - pe_range[0]) * u[2]
+    u = uniform01(seed, STREAM_VEL, 64)
+    for q in range(0, 62, 2):
+        x1, x2 = 2.0 * u[q] - 1.0, 2.0 * u[q + 1] - 1.0
+        s2 = x1 * x1 + x2 * x2
+        if 0.0 < s2 < 1.0:
+            break
+    r = 2.0 * np.sqrt(1.0 - s2)
+    v = np.array([x1 * r, x2 * r, 1.0 - 2.0 * s2])
+    pe = pe_range[0] + (pe_range[1] - pe_range[0]) * u[63]
     c = pe * np.abs(v)
     offs = [-m * m, -m, -1, 0, 1, m, m * m]
     axis = [2, 1, 0, None, 0, 1, 2]
@@ -240,7 +292,10 @@ def batched_sides(count: int, seed: int, lo: int = 16, hi: int = 128):
 def serving_sides(count: int, seed: int, lo: int = 20, hi: int = 160):
     """Per-request grid sides, log-uniform on [lo, hi] (so unknowns log-uniform too)."""
     u = uniform01(seed, STREAM_COEF, count)
-    return np.rint(np.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * u)).astype(np.int64)
+    span = _ln_det(hi / lo)
+    if not (0.0 <= span < 2.5):
+        raise ValueError("serving sides need 1 <= hi / lo < 12")
+    return np.rint(lo * _exp_small(span * u)).astype(np.int64)
 
 
 @dataclass

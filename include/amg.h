@@ -91,6 +91,12 @@ typedef struct {
                               finest level excluded) as one cooperative launch with grid-wide
                               barriers; applies when npre = npost = 1.  Off by default: inside
                               the solve's CUDA graph the separate launches were faster. */
+    int device_setup;      /* [1] build the hierarchy on the GPU: strength of connection,
+                              aggregation, smoothed prolongation, R = P^T and the Galerkin
+                              product run as kernels and the level matrices stay on the
+                              device; 0 = the graph steps on host threads (the Galerkin
+                              product stays on the GPU).  Both give the same hierarchy, bit
+                              for bit. */
 } amg_params;
 
 /* A CSR matrix as passed in by the caller (see the conventions above). */
@@ -150,6 +156,18 @@ const char *amg_last_error(void);
  * the coarsest level).  Any output may be NULL. */
 amg_status amg_hierarchy_info(const amg_handle *h, int *levels, int64_t *rows, int64_t *nnz_a,
                               int64_t *nnz_p);
+
+/* Algorithmic bytes of one Krylov iteration on this hierarchy, the roofline
+ * numerator of the solve (Sec. 3: the solve phase is sparse products and
+ * vector updates, bound by memory bandwidth).  Model: every array a kernel
+ * reads or writes counts once per kernel and the gathered vector once;
+ * 12 bytes per float64 nonzero (8 value + 4 column; 8 for float32 values,
+ * 6 for bfloat16), 4 per row pointer, 8 (4) per float64 (float32) vector
+ * entry.  Per V-cycle level: pre-sweep with residual, restriction,
+ * prolongation with correction, post-sweep; the dense coarsest solve reads
+ * its inverse.  CG adds q = A p with p.q (12 Z0 + 20 n0) and the x, r, p
+ * updates (72 n0); BiCGStab two V-cycles, two products and 136 n0. */
+amg_status amg_hierarchy_bytes(const amg_handle *h, double *bytes_per_iteration);
 
 /* Copy level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l) of level l to host
  * arrays sized from amg_hierarchy_info: row_ptr (rows + 1), col and val (nnz).
@@ -219,6 +237,10 @@ amg_status amg_batch_tune(amg_batch *b, const double *f, double *x, double rtol,
 /* total_rows: sum of the systems' sizes; row_off: nsys + 1 offsets of the
  * systems in f and x; levels: nsys level counts.  Outputs may be NULL. */
 amg_status amg_batch_info(const amg_batch *b, int64_t *total_rows, int64_t *row_off, int *levels);
+
+/* Algorithmic bytes of one CG iteration of each system (nsys doubles), by
+ * the model of amg_hierarchy_bytes, for the batch's precision. */
+amg_status amg_batch_bytes(const amg_batch *b, double *bytes_per_iteration);
 
 /* Release the batch and its device memory.  NULL is accepted. */
 amg_status amg_batch_free(amg_batch *b);
@@ -307,6 +329,10 @@ amg_status amg_server_wait(amg_server *s, int64_t id, double *x_host, int *iters
  * may be NULL. */
 amg_status amg_server_stats(amg_server *s, int64_t *completed, int *resident_count, int64_t *resident_bytes,
                             int64_t *peak_bytes, int64_t *evictions);
+
+/* Algorithmic bytes moved by the solves the server finished so far: for
+ * each solve, amg_hierarchy_bytes of its hierarchy times its iterations. */
+amg_status amg_server_solve_bytes(amg_server *s, double *bytes);
 
 /* Finish every queued request, stop the workers and free the resident
  * hierarchies.  Results not yet collected are dropped.  NULL is accepted. */

@@ -51,6 +51,7 @@ class amg_params(C.Structure):
         ("use_stream", C.c_int),
         ("use_pdl", C.c_int),
         ("use_tail", C.c_int),
+        ("device_setup", C.c_int),
     ]
 
 
@@ -82,6 +83,9 @@ _sigs = {
     "amg_spmv_dot_noalloc": [C.POINTER(amg_csr), _VP, _VP, _VP, _VP],
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
+    "amg_hierarchy_bytes": [_VP, C.POINTER(_D)],
+    "amg_batch_bytes": [_VP, _VP],
+    "amg_server_solve_bytes": [_VP, C.POINTER(_D)],
     "amg_last_solve_mode": [_VP, C.POINTER(_I), C.POINTER(_I)],
     "amg_check_wait_limit": [C.POINTER(_D)],
     "amg_batch_setup": [_I, _VP, C.POINTER(amg_params), _VP, C.POINTER(_VP)],
@@ -294,6 +298,24 @@ def amg_batch_setup(systems, params: amg_params = None, stream=None):
     _check(_lib.amg_batch_setup(len(systems), C.cast(arr, C.c_void_p), p, _stream(stream), C.byref(h)),
            "amg_batch_setup")
     return h
+
+
+def amg_hierarchy_bytes(h) -> float:
+    v = C.c_double()
+    _check(_lib.amg_hierarchy_bytes(h, C.byref(v)), "amg_hierarchy_bytes")
+    return v.value
+
+
+def amg_batch_bytes(b, nsys):
+    out = np.zeros(nsys, np.float64)
+    _check(_lib.amg_batch_bytes(b, out.ctypes.data), "amg_batch_bytes")
+    return out
+
+
+def amg_server_solve_bytes(srv) -> float:
+    v = C.c_double()
+    _check(_lib.amg_server_solve_bytes(srv, C.byref(v)), "amg_server_solve_bytes")
+    return v.value
 
 
 def amg_batch_info(b, nsys):

@@ -19,7 +19,7 @@ LIB_NAME = "libamg_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["spmv.cu", "spgemm.cu", "solver.cu", "capi.cu", "noalloc.cu", "tail.cu", "batch.cu"]
+CU_SOURCES = ["spmv.cu", "spgemm.cu", "solver.cu", "capi.cu", "noalloc.cu", "tail.cu", "batch.cu", "setup_dev.cu"]
 CPP_SOURCES = ["setup_host.cpp", "batch_host.cpp", "server.cpp"]
 
 

@@ -51,6 +51,18 @@ std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_c
 std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, int rows_cap_max,
                                 int& vw, int& rows_cap);
 
+// Algorithmic bytes of one Krylov iteration on a hierarchy with these level
+// sizes (rows, nonzeros of A_l, nonzeros of P_l): every array a kernel reads
+// or writes counted once per kernel, the gathered vector once; int32 columns
+// and row pointers, V-cycle values of the precision's width (8, 4 or 2
+// bytes) with level vectors of 8 or 4 bytes; the outer product q = A p and
+// the Krylov vector updates in float64.  CG: one V-cycle, one product and
+// the updates of x, r, p; BiCGStab: two of each and its longer updates.
+struct LevelSizes {
+    int64_t n, nnz, nnz_p;
+};
+double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver);
+
 // ---------------------------------------------------------- device CSR
 // Row-block schedule: block b of the SpMV kernel covers rows
 // [blk[b], blk[b+1]); at most kRowsPerBlock rows and (unless a single row)
@@ -233,6 +245,18 @@ int* dev_err_ptr();
 // Runs the bounded-wait check kernel on the current device; returns the device
 // error word it left (cleared afterwards) and the kernel's duration.
 int check_wait_limit(double* seconds);
+
+// Device set-up of one level (setup_dev.cu); the same results, bit for bit,
+// as the host functions above.  dev_prolongation and dev_transpose allocate
+// the output matrix's arrays (stream-ordered, kPad padding).
+void dev_diagonal(const DevCsr& A, double* dg, cudaStream_t s);  // fails on a zero / missing diagonal
+void dev_smoother_diag(const DevCsr& A, const double* dg, const amg_params& prm, double* d, cudaStream_t s);
+void dev_scale_columns(const DevCsr& A, const double* d, double* out, cudaStream_t s);  // a_ij d_j
+int64_t dev_aggregate(const DevCsr& A, const double* dg, double eps, int32_t* agg, uint8_t* strong,
+                      cudaStream_t s);
+void dev_prolongation(const DevCsr& A, const double* dg, const uint8_t* strong, const int32_t* agg,
+                      int64_t nagg, DevCsr& P, double& omega, cudaStream_t s);
+void dev_transpose(const DevCsr& P, DevCsr& R, cudaStream_t s);
 
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.

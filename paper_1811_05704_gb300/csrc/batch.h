@@ -81,6 +81,7 @@ struct amg_batch {
     std::vector<int64_t> row_off;     // nsys + 1
     std::vector<int> levels;          // per system
     std::vector<int64_t> nnz_fine;    // per system
+    std::vector<double> iter_bytes;   // per system: algorithmic bytes of one CG iteration
     amg::BSys* sys = nullptr;         // device descriptors
     int64_t* row_off_dev = nullptr;
     int* order_by_size = nullptr;     // device: largest system first

@@ -270,11 +270,18 @@ void build_batch(amg_batch* b, const amg_csr* systems) {
     b->row_off.assign(ns + 1, 0);
     b->levels.resize(ns);
     b->nnz_fine.resize(ns);
+    b->iter_bytes.resize(ns);
     for (int k = 0; k < ns; ++k) {
         HSys& S = sys[k];
         SOff& o = off[k];
         const int L = (int)S.A.size();
         const HostCsr& A0 = S.A[0];
+        {
+            std::vector<LevelSizes> sz(L);
+            for (int l = 0; l < L; ++l)
+                sz[l] = {S.A[l].nrows, S.A[l].nnz(), l + 1 < L ? S.P[l].nnz() : 0};
+            b->iter_bytes[k] = krylov_iteration_bytes(sz, prm.precision, AMG_SOLVER_CG);
+        }
         b->row_off[k + 1] = b->row_off[k] + A0.nrows;
         b->levels[k] = L;
         b->nnz_fine[k] = A0.nnz();

@@ -190,6 +190,7 @@ amg_status amg_params_default(amg_params* p) {
     p->use_stream = 1;
     p->use_pdl = 1;
     p->use_tail = 0;
+    p->device_setup = 1;
     return AMG_OK;
 }
 
@@ -382,6 +383,17 @@ amg_status amg_hierarchy_info(const amg_handle* h, int* levels, int64_t* rows, i
     });
 }
 
+amg_status amg_hierarchy_bytes(const amg_handle* h, double* bytes_per_iteration) {
+    return guarded([&]() -> amg_status {
+        if (!h || !bytes_per_iteration) fail(AMG_ERR_INVALID_ARG, "null argument");
+        std::vector<LevelSizes> sz(h->lev.size());
+        for (size_t l = 0; l < h->lev.size(); ++l)
+            sz[l] = {h->lev[l].A.nrows, h->lev[l].A.nnz, l + 1 < h->lev.size() ? h->lev[l].P.nnz : 0};
+        *bytes_per_iteration = krylov_iteration_bytes(sz, h->prm.precision, h->prm.solver);
+        return AMG_OK;
+    });
+}
+
 amg_status amg_get_level_matrix(const amg_handle* h, int level, int which, int32_t* row_ptr,
                                 int32_t* col, double* val) {
     return guarded([&]() -> amg_status {
@@ -404,7 +416,12 @@ amg_status amg_get_aggregates(const amg_handle* h, int level, int32_t* agg) {
         const Level& L = level_of(h, level);
         if (level + 1 >= (int)h->lev.size()) fail(AMG_ERR_INVALID_ARG, "the coarsest level has no aggregates");
         if (!agg) fail(AMG_ERR_INVALID_ARG, "null output");
-        std::memcpy(agg, L.agg.data(), L.agg.size() * sizeof(int32_t));
+        if (L.agg_dev) {
+            AMG_CUDA(cudaMemcpyAsync(agg, L.agg_dev, L.A.nrows * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+        } else {
+            std::memcpy(agg, L.agg.data(), L.agg.size() * sizeof(int32_t));
+        }
         return AMG_OK;
     });
 }
@@ -413,7 +430,12 @@ amg_status amg_get_smoother_diag(const amg_handle* h, int level, double* d) {
     return guarded([&]() -> amg_status {
         const Level& L = level_of(h, level);
         if (!d) fail(AMG_ERR_INVALID_ARG, "null output");
-        std::memcpy(d, L.dhost.data(), L.dhost.size() * sizeof(double));
+        if (L.dhost.empty()) {
+            AMG_CUDA(cudaMemcpyAsync(d, L.d, L.A.nrows * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+        } else {
+            std::memcpy(d, L.dhost.data(), L.dhost.size() * sizeof(double));
+        }
         return AMG_OK;
     });
 }
@@ -592,6 +614,14 @@ amg_status amg_batch_info(const amg_batch* b, int64_t* total_rows, int64_t* row_
             if (row_off) row_off[k] = b->row_off[k];
             if (levels && k < b->nsys) levels[k] = b->levels[k];
         }
+        return AMG_OK;
+    });
+}
+
+amg_status amg_batch_bytes(const amg_batch* b, double* bytes_per_iteration) {
+    return guarded([&]() -> amg_status {
+        if (!b || !bytes_per_iteration) fail(AMG_ERR_INVALID_ARG, "null argument");
+        for (int k = 0; k < b->nsys; ++k) bytes_per_iteration[k] = b->iter_bytes[k];
         return AMG_OK;
     });
 }

@@ -19,8 +19,9 @@ struct Level {
     // iterate, y post-smoothed output, t residual
     double *f = nullptr, *x = nullptr, *y = nullptr, *t = nullptr;
     float *f32 = nullptr, *x32 = nullptr, *y32 = nullptr, *t32 = nullptr;
-    std::vector<int32_t> agg;   // host copy of the aggregates (non-coarsest)
-    std::vector<double> dhost;  // host copy of the smoother diagonal
+    std::vector<int32_t> agg;   // host copy of the aggregates (non-coarsest, host set-up)
+    int32_t* agg_dev = nullptr; // device aggregates (non-coarsest, device set-up)
+    std::vector<double> dhost;  // host copy of the smoother diagonal (host set-up)
     int64_t nagg = 0;
     double omega_p = 0.0;
 };

@@ -90,6 +90,7 @@ struct amg_server {
     int64_t peak = 0;
     int64_t completed = 0;
     int64_t evictions = 0;
+    double solve_bytes = 0.0;  // algorithmic bytes of the finished solves
     int running = 0;
     std::atomic<int> setups{0};  // set-ups running now (their host steps share the cores)
     bool stop = false;
@@ -257,9 +258,13 @@ void worker(amg_server* s) {
         }
         // a hierarchy whose solve hit a device error is not kept
         const bool keep = h && status != AMG_ERR_CUDA && status != AMG_ERR_OOM;
+        double bytes = 0.0;
+        if (h && (status == AMG_OK || status == AMG_ERR_NOT_CONVERGED) && amg_hierarchy_bytes(h, &bytes) == AMG_OK)
+            bytes *= r->iters;
         amg_handle* to_free = nullptr;
         {
             std::lock_guard<std::mutex> lk(s->m);
+            s->solve_bytes += bytes;
             if (reuse) {
                 auto it = s->resident.find(r->key);
                 if (keep) {
@@ -385,6 +390,13 @@ amg_status amg_server_stats(amg_server* s, int64_t* completed, int* resident_cou
     if (resident_bytes) *resident_bytes = rb;
     if (peak_bytes) *peak_bytes = s->peak;
     if (evictions) *evictions = s->evictions;
+    return AMG_OK;
+}
+
+amg_status amg_server_solve_bytes(amg_server* s, double* bytes) {
+    if (!s || !bytes) return AMG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->m);
+    *bytes = s->solve_bytes;
     return AMG_OK;
 }
 

@@ -462,4 +462,27 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
     return out;
 }
 
+double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver) {
+    if (lev.empty()) return 0.0;
+    const double e = precision == AMG_PRECISION_BF16 ? 6.0 : precision == AMG_PRECISION_FP32 ? 8.0 : 12.0;
+    const double v = precision == AMG_PRECISION_FP64 ? 8.0 : 4.0;
+    const size_t L = lev.size();
+    double vc = 0.0;  // one V-cycle
+    for (size_t l = 0; l + 1 < L; ++l) {
+        const double n = (double)lev[l].n, z = (double)lev[l].nnz, zp = (double)lev[l].nnz_p;
+        const double nc = (double)lev[l + 1].n;
+        vc += e * z + 4 * n + 4 * v * n;             // pre-sweep + residual: d, f read; x, t written
+        vc += e * zp + 4 * nc + v * n + v * nc;      // restriction: t gathered, f_{l+1} written
+        vc += e * zp + 4 * n + v * nc + 2 * v * n;   // prolongation + correction
+        vc += e * z + 4 * n + 4 * v * n;             // post-sweep: x gathered, d, f read, y written
+    }
+    const double nL = (double)lev[L - 1].n;
+    vc += 8 * nL * nL + 2 * v * nL;                  // dense coarsest solve (float64 inverse)
+    const double n0 = (double)lev[0].n, z0 = (double)lev[0].nnz;
+    const double spmv = 12 * z0 + 4 * n0 + 16 * n0;  // q = A p with a dot product
+    if (solver == AMG_SOLVER_BICGSTAB)
+        return 2 * vc + 2 * spmv + 136 * n0;         // p, s, x, r updates and the extra dots
+    return vc + spmv + 72 * n0;                      // x, r update with ||r||; p = z + beta p
+}
+
 }  // namespace amg

@@ -163,12 +163,146 @@ static void build_tail(amg_handle* h) {
     h->tail_ls = ls;
 }
 
+// Level vectors of every level and the tail plan (both set-up paths).
+static void finish_hierarchy(amg_handle* h);
+
+// Row pointers of a device matrix on the host (for the launch schedules).
+static std::vector<int32_t> download_ptr(const DevCsr& D, cudaStream_t s) {
+    std::vector<int32_t> p(D.nrows + 1);
+    AMG_CUDA(cudaMemcpyAsync(p.data(), D.ptr, (D.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    return p;
+}
+
+// float32 / bfloat16 copies of a level's matrix values, scaled values and
+// smoother diagonal (mixed-precision V-cycles), from the device copies.
+static void make_level_f32(amg_handle* h, Level& L, int64_t n) {
+    make_f32(h, L.A);
+    if (h->prm.precision == AMG_PRECISION_BF16) {
+        L.A.vald16 = halloc<uint16_t>(h, L.A.nnz + kPad);
+        AMG_CUDA(cudaMemsetAsync(L.A.vald16, 0, (L.A.nnz + kPad) * sizeof(uint16_t), h->stream));
+        launch_copy_to_bf16(L.A.vald, L.A.vald16, L.A.nnz, h->stream);
+    } else {
+        L.A.vald32 = halloc<float>(h, L.A.nnz + kPad);
+        AMG_CUDA(cudaMemsetAsync(L.A.vald32, 0, (L.A.nnz + kPad) * sizeof(float), h->stream));
+        launch_copy_to_f32(L.A.vald, L.A.vald32, L.A.nnz, h->stream);
+    }
+    L.d32 = halloc<float>(h, n + kPad);
+    AMG_CUDA(cudaMemsetAsync(L.d32, 0, (n + kPad) * sizeof(float), h->stream));
+    launch_copy_to_f32(L.d, L.d32, n, h->stream);
+}
+
+// Algorithm 1 on the GPU: the level matrices never leave the device; the host
+// reads back only row pointers (for the launch schedules), the aggregate
+// count and damping factor of each level, and the coarsest matrix (for its
+// dense inverse).  Same stop rule and the same hierarchy, bit for bit, as the
+// host set-up below.
+static void build_hierarchy_dev(amg_handle* h, const HostCsr& A0) {
+    const amg_params& prm = h->prm;
+    const bool f32 = prm.precision != AMG_PRECISION_FP64;
+    cudaStream_t s = h->stream;
+    h->lev.clear();
+    h->lev.reserve(AMG_MAX_LEVELS + 1);
+    h->lev.emplace_back();
+    upload(h, A0, h->lev[0].A, kRowsPerBlock);
+    for (int l = 0;; ++l) {
+        Level& L = h->lev[l];
+        const int64_t n = L.A.nrows;
+        double* dg = dev_alloc_async<double>(n, s);
+        uint8_t* strong = nullptr;
+        auto release = [&]() {
+            if (dg) dev_free_async(dg, s);
+            if (strong) dev_free_async(strong, s);
+            dg = nullptr;
+            strong = nullptr;
+        };
+        try {
+            dev_diagonal(L.A, dg, s);
+            L.d = halloc<double>(h, n + kPad);
+            AMG_CUDA(cudaMemsetAsync(L.d, 0, (n + kPad) * sizeof(double), s));
+            dev_smoother_diag(L.A, dg, prm, L.d, s);
+            L.A.vald = halloc<double>(h, L.A.nnz + kPad);
+            AMG_CUDA(cudaMemsetAsync(L.A.vald, 0, (L.A.nnz + kPad) * sizeof(double), s));
+            dev_scale_columns(L.A, L.d, L.A.vald, s);
+            bool coarsest = n <= prm.coarse_enough || l + 1 >= prm.max_levels || l + 1 >= AMG_MAX_LEVELS;
+            if (!coarsest) {
+                double eps = prm.strength_eps;
+                if (prm.strength_halving)
+                    for (int q = 0; q < l; ++q) eps *= 0.5;
+                strong = dev_alloc_async<uint8_t>(L.A.nnz > 0 ? L.A.nnz : 1, s);
+                L.agg_dev = halloc<int32_t>(h, n);
+                L.nagg = dev_aggregate(L.A, dg, eps, L.agg_dev, strong, s);
+                if ((double)L.nagg >= 0.95 * (double)n) {
+                    L.nagg = 0;
+                    L.agg_dev = nullptr;  // freed with the handle
+                    if (n > prm.max_coarse_dense)
+                        fail(AMG_ERR_COARSENING_STALLED,
+                             "aggregation stalled on level " + std::to_string(l) + " with " +
+                                 std::to_string(n) + " rows");
+                    coarsest = true;
+                } else {
+                    dev_prolongation(L.A, dg, strong, L.agg_dev, L.nagg, L.P, L.omega_p, s);
+                    track(h, L.P);
+                    release();
+                    dev_transpose(L.P, L.R, s);
+                    track(h, L.R);
+                    schedule(h, download_ptr(L.P, s), L.P, 2 * kRowsPerBlock);
+                    schedule(h, download_ptr(L.R, s), L.R, 2 * kRowsPerBlock);
+                    DevCsr AP, Ac;
+                    device_spgemm(L.A, L.P, AP, s);
+                    auto free_ap = [&]() {
+                        dev_free_async(AP.ptr, s);
+                        dev_free_async(AP.col, s);
+                        dev_free_async(AP.val, s);
+                    };
+                    try {
+                        device_spgemm(L.R, AP, Ac, s);
+                    } catch (...) {
+                        free_ap();
+                        throw;
+                    }
+                    free_ap();
+                    track(h, Ac);
+                    schedule(h, download_ptr(Ac, s), Ac, kRowsPerBlock);
+                    if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
+                    h->lev.emplace_back();
+                    h->lev.back().A = Ac;
+                }
+            }
+            release();
+            if (f32) make_level_f32(h, h->lev[l], n);
+            if (coarsest) {
+                Level& C = h->lev[l];
+                if (n > prm.max_coarse_dense)
+                    fail(AMG_ERR_TOO_LARGE, "coarsest level has " + std::to_string(n) +
+                                                " rows, above max_coarse_dense");
+                HostCsr H;
+                download(C.A, H, s);
+                std::vector<double> inv;
+                host_dense_inverse(H, inv);
+                h->nc = (int32_t)n;
+                h->cinv = halloc<double>(h, inv.size());
+                AMG_CUDA(cudaMemcpyAsync(h->cinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+                break;
+            }
+        } catch (...) {
+            release();
+            throw;
+        }
+    }
+    finish_hierarchy(h);
+}
+
 // ------------------------------------------------------------- setup
 // Algorithm 1.  Stop rule: a level with at most coarse_enough rows, the
 // max_levels-th level, or a level whose aggregation keeps >= 95% of the rows
 // is the coarsest; a stall on a level larger than max_coarse_dense is an
 // error, and so is a coarsest level larger than max_coarse_dense.
 void build_hierarchy(amg_handle* h, HostCsr A) {
+    if (h->prm.device_setup) {
+        build_hierarchy_dev(h, A);
+        return;
+    }
     const amg_params& prm = h->prm;
     const bool f32 = prm.precision != AMG_PRECISION_FP64;  // float32 V-cycle (values fp32 or bf16)
     h->lev.clear();
@@ -264,6 +398,11 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
             break;
         }
     }
+    finish_hierarchy(h);
+}
+
+static void finish_hierarchy(amg_handle* h) {
+    const bool f32 = h->prm.precision != AMG_PRECISION_FP64;
     // level vectors
     const int nl = (int)h->lev.size();
     for (int l = 0; l < nl; ++l) {

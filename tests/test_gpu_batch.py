@@ -121,3 +121,18 @@ def test_batch_full_size_4096(amg):
         assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
         assert it[k] <= ito + 3
     amg.amg_batch_free(b)
+
+
+def test_iteration_bytes_agree_with_single_system(amg):
+    """amg_batch_bytes gives each system the bytes per CG iteration that
+    amg_hierarchy_bytes gives the same matrix set up alone (same hierarchy,
+    same precision)."""
+    mats, rhs = _systems(6, 5, lo=20, hi=60)
+    for precision in (0, 1):
+        b, st, it, rr, sst, x, off, lev = _run(amg, mats, rhs, precision=precision)
+        per = amg.amg_batch_bytes(b, len(mats))
+        amg.amg_batch_free(b)
+        for A, v in zip(mats, per):
+            S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=precision)
+            assert v == amg.amg_hierarchy_bytes(S.handle) > 0
+            S.close()

@@ -60,7 +60,7 @@ def _alone(amg, reqs, seed):
         f = q.rhs(seed, A.n)
         x = np.zeros(A.n)
         st, it, rr = amg.amg_solve_host(handles[q.key], f, x, RTOL, 300)
-        out.append((st, x, it, rr))
+        out.append((st, x, it, rr, amg.amg_hierarchy_bytes(handles[q.key]) * it))
     for h in handles.values():
         amg.amg_free(h)
     return mats, out
@@ -80,7 +80,7 @@ def test_served_results_equal_alone(amg):
     srv = amg.amg_server_create(slots=4)
     # reused keys are submitted without their matrix half of the time
     ids = [_submit(amg, srv, q, mats, seed, with_matrix=not (q.reuse and q.index % 2)) for q in reqs]
-    for q, rid, (st0, x0, it0, rr0) in zip(reqs, ids, alone):
+    for q, rid, (st0, x0, it0, rr0, _) in zip(reqs, ids, alone):
         st, x, it, rr, lat, qt = amg.amg_server_wait(srv, rid, mats[q.key].n)
         assert st == st0 == 0, (q, amg.amg_last_error())
         assert it == it0 and rr == rr0, q
@@ -89,6 +89,9 @@ def test_served_results_equal_alone(amg):
     stats = amg.amg_server_stats(srv)
     assert stats["completed"] == len(reqs)
     assert stats["resident_count"] == len({q.key for q in reqs}) and stats["evictions"] == 0
+    # the server's byte count is the sum of the same solves' counts alone
+    want = sum(a[4] for a in alone)
+    assert abs(amg.amg_server_solve_bytes(srv) - want) <= 1e-12 * want and want > 0
     amg.amg_server_destroy(srv)
 
 
