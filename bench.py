@@ -119,24 +119,32 @@ def gather_lists(items, world):
 def kernel_bytes(info):
     """Algorithmic DRAM bytes per launch of each finest-level kernel (FP64 values,
     int32 indices and row pointers; every array touched once per kernel, the
-    gathered vector counted once)."""
+    gathered vector counted once).  With the fused restriction operator M on
+    the finest level (info["nnz_m"][0] > 0) the restriction kernel is f_1 = M r
+    and the prolongation forms x = d r + P x_1; there is no pre-sweep kernel."""
     n0, z0 = info["rows"][0], info["nnz"][0]
     n1 = info["rows"][1] if info["levels"] > 1 else 0
-    zp = info["nnz_p"][0]
-    return {
+    zp, zm = info["nnz_p"][0], info["nnz_m"][0]
+    out = {
         "spmv_dot": 12 * z0 + 4 * n0 + 8 * n0 + 8 * n0,           # A, row_ptr, p, q
         "presmooth_l0": 12 * z0 + 4 * n0 + 16 * n0 + 16 * n0,     # A, d f read, x t written
         "restrict_l0": 12 * zp + 4 * n1 + 8 * n0 + 8 * n1,        # R, t, f_1
         "prolong_l0": 12 * zp + 4 * n0 + 8 * n1 + 16 * n0,        # P, x_1, x read+write
         "postsmooth_l0": 12 * z0 + 4 * n0 + 8 * n0 + 16 * n0 + 8 * n0,  # A, x, d f, z
     }
+    if zm:
+        del out["presmooth_l0"]
+        out["restrict_l0"] = 12 * zm + 4 * n1 + 8 * n0 + 8 * n1   # M, r gathered, f_1
+        out["prolong_l0"] = 12 * zp + 4 * n0 + 8 * n1 + 24 * n0   # P, x_1, d r read, x written
+    return out
 
 
 def kernel_bytes_mixed(info, vb):
     """As kernel_bytes for the float32 V-cycle with vb-byte matrix values (4:
     float32, 2: bfloat16): float32 level vectors; the finest level reads the
     Krylov vector as the float32 copy the Krylov kernels write, and writes z
-    in float64 with the float64 dot product r.z."""
+    in float64 with the float64 dot product r.z.  (The float V-cycles do not
+    use the fused restriction operator.)"""
     n0, z0 = info["rows"][0], info["nnz"][0]
     n1 = info["rows"][1] if info["levels"] > 1 else 0
     zp = info["nnz_p"][0]
@@ -161,14 +169,19 @@ def kernel_flops(info):
     """FP64 operations per launch of each finest-level kernel (a fused
     multiply-add counts 2)."""
     n0, z0 = info["rows"][0], info["nnz"][0]
-    zp = info["nnz_p"][0]
-    return {
+    zp, zm = info["nnz_p"][0], info["nnz_m"][0]
+    out = {
         "spmv_dot": 2 * z0 + 2 * n0,              # A p, p.q
         "presmooth_l0": 2 * z0 + 2 * n0,          # A (d f) on scaled values, x = d f, t = f - s
         "restrict_l0": 2 * zp,                    # R t
         "prolong_l0": 2 * zp + n0,                # x += P x_1
         "postsmooth_l0": 2 * z0 + 5 * n0,         # A x, f - s, x + d (.), f.y
     }
+    if zm:
+        del out["presmooth_l0"]
+        out["restrict_l0"] = 2 * zm               # M r
+        out["prolong_l0"] = 2 * zp + 2 * n0       # d r + P x_1
+    return out
 
 
 def bytes_per_iteration(info, coarse_n):
@@ -177,9 +190,14 @@ def bytes_per_iteration(info, coarse_n):
     L = info["levels"]
     for l in range(L - 1):
         n, z, zp, nc = info["rows"][l], info["nnz"][l], info["nnz_p"][l], info["rows"][l + 1]
-        b += 12 * z + 4 * n + 32 * n                 # presmooth + residual
-        b += 12 * zp + 4 * nc + 8 * n + 8 * nc       # restrict
-        b += 12 * zp + 4 * n + 8 * nc + 16 * n       # prolong + correct
+        zm = info["nnz_m"][l]
+        if zm:
+            b += 12 * zm + 4 * nc + 8 * n + 8 * nc   # f_{l+1} = M f
+            b += 12 * zp + 4 * n + 8 * nc + 24 * n   # x = d f + P x_{l+1}
+        else:
+            b += 12 * z + 4 * n + 32 * n             # presmooth + residual
+            b += 12 * zp + 4 * nc + 8 * n + 8 * nc   # restrict
+            b += 12 * zp + 4 * n + 8 * nc + 16 * n   # prolong + correct
         b += 12 * z + 4 * n + 32 * n                 # postsmooth
     b += 8 * coarse_n * coarse_n + 16 * coarse_n     # dense coarsest solve
     n0, z0 = info["rows"][0], info["nnz"][0]
@@ -533,7 +551,10 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
                     time.sleep(delay)
             ids.append(amg.amg_server_submit(srv, q.key, csrs[(q.kind, q.side)], rhs[q.index], prm_of(q),
                                              RTOL, MAXITER))
-        res = [amg.amg_server_wait(srv, rid, A_of(q).n) for q, rid in zip(reqs, ids)]
+        res = []
+        for q, rid in zip(reqs, ids):
+            r = amg.amg_server_wait(srv, rid, A_of(q).n)
+            res.append(r + ((amg.amg_last_error() if r[0] != 0 else ""),))
         wall = time.perf_counter() - t_start
         stats = amg.amg_server_stats(srv)
         stats["solve_bytes"] = amg.amg_server_solve_bytes(srv)
@@ -552,8 +573,8 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
     moved = float(sum(gather_lists([float(sat_stats["solve_bytes"])], world)))
     ok = all(r[0] == 0 and r[3] <= RTOL for r in sat_res + open_res) and all(s == 0 for s in serial_status.values())
     ok = all(gather_lists([ok], world))
-    failed = [{"index": q.index, "kind": q.kind, "side": q.side, "status": [r[0], o[0], serial_status[q.index]],
-               "iters": r[2], "relres": r[3]}
+    failed = [{"index": q.index, "kind": q.kind, "side": q.side, "status": [r[0], o[0], serial_status.get(q.index)],
+               "iters": r[2], "relres": r[3], "error": r[6] or o[6]}
               for q, r, o in zip(reqs, sat_res, open_res)
               if r[0] != 0 or o[0] != 0 or serial_status.get(q.index, 0) != 0 or r[3] > RTOL][:10]
     failed = gather_lists(failed, world)[:10]
@@ -610,6 +631,7 @@ def main():
     S = amg.Solver(A.n, A.row_ptr, A.col, A.val)
     setup_s = time.perf_counter() - t0
     info = S.info()
+    info["nnz_m"] = [amg.amg_fused_restriction_nnz(S.handle, l) for l in range(info["levels"])]
     coarse_n = info["rows"][-1]
     ft = torch.from_numpy(f).to(dev)
     x = torch.zeros(A.n, dtype=torch.float64, device=dev)

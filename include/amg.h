@@ -169,11 +169,21 @@ amg_status amg_hierarchy_info(const amg_handle *h, int *levels, int64_t *rows, i
  * updates (72 n0); BiCGStab two V-cycles, two products and 136 n0. */
 amg_status amg_hierarchy_bytes(const amg_handle *h, double *bytes_per_iteration);
 
-/* Copy level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l) of level l to host
- * arrays sized from amg_hierarchy_info: row_ptr (rows + 1), col and val (nnz).
- * P and R do not exist on the coarsest level (INVALID_ARG). */
+/* Copy level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l, 3 = M_l) of level l
+ * to host arrays sized from amg_hierarchy_info (amg_fused_restriction_nnz
+ * for M_l): row_ptr (rows + 1), col and val (nnz).  P, R and M do not exist
+ * on the coarsest level, M only where the level uses it (INVALID_ARG). */
 amg_status amg_get_level_matrix(const amg_handle *h, int level, int which, int32_t *row_ptr,
                                 int32_t *col, double *val);
+
+/* Nonzeros of the fused restriction operator of level l, 0 if the level does
+ * not use one (Algorithm 2's pre-smoothing from a zero guess, residual and
+ * restriction, composed: with one pre-sweep x = d f, the restricted residual
+ * is R (f - A D f) = M f, M = R - R A D, D = diag(d).  The set-up forms M
+ * where one product with it moves fewer bytes than the three steps, and the
+ * V-cycle then computes f_{l+1} = M f going down and x = d f + P x_{l+1}
+ * coming up.  Only for the float64 V-cycle, with npre = 1 and use_tail = 0.) */
+amg_status amg_fused_restriction_nnz(const amg_handle *h, int level, int64_t *nnz);
 
 /* Aggregate id of every row of level l (host array of rows[l] entries);
  * INVALID_ARG on the coarsest level. */
@@ -257,8 +267,11 @@ amg_status amg_batch_free(amg_batch *b);
  * the matrix may span at most 65,536 row blocks (n up to 16,777,216 rows when
  * rows average at most 8 nonzeros; fewer rows for longer rows); above that
  * the call returns AMG_ERR_TOO_LARGE.  The first call on a device looks up
- * the array's device address (make that first call before any stream
- * capture).  All calls in the process share the one array, and it keeps the
+ * the array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture, since the look-up is a runtime call outside any
+ * stream.  Every call then waits on its stream twice, to read back the checks
+ * of the row pointers and of the column indices.  All calls in the process
+ * share the one array, and it keeps the
  * previous call's contents (the call clears what must start at zero): calls
  * that overlap on the GPU race and must be ordered by the caller.  Results
  * are identical to amg_spmv_dot's.  Errors: INVALID_ARG, TOO_LARGE, CUDA. */

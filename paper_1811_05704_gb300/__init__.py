@@ -84,6 +84,7 @@ _sigs = {
     "amg_solve_profile": [_VP, _VP, _VP, _D, _I, C.POINTER(_I), C.POINTER(_D), _VP, _VP],
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
     "amg_hierarchy_bytes": [_VP, C.POINTER(_D)],
+    "amg_fused_restriction_nnz": [_VP, _I, C.POINTER(_I64)],
     "amg_batch_bytes": [_VP, _VP],
     "amg_server_solve_bytes": [_VP, C.POINTER(_D)],
     "amg_last_solve_mode": [_VP, C.POINTER(_I), C.POINTER(_I)],
@@ -236,15 +237,22 @@ def amg_hierarchy_info(h):
     return dict(levels=L, rows=rows[:L].tolist(), nnz=nnz[:L].tolist(), nnz_p=nnzp[:L].tolist())
 
 
+def amg_fused_restriction_nnz(h, level) -> int:
+    v = C.c_int64()
+    _check(_lib.amg_fused_restriction_nnz(h, level, C.byref(v)), "amg_fused_restriction_nnz")
+    return v.value
+
+
 def amg_get_level_matrix(h, level, which):
-    """which in {'A','P','R'} -> (row_ptr int32, col int32, val float64, shape)."""
+    """which in {'A','P','R','M'} -> (row_ptr int32, col int32, val float64, shape)."""
     info = amg_hierarchy_info(h)
-    w = {"A": 0, "P": 1, "R": 2}[which]
+    w = {"A": 0, "P": 1, "R": 2, "M": 3}[which]
     n = info["rows"][level]
     nc = info["rows"][level + 1] if level + 1 < info["levels"] else 0
-    nrows = nc if which == "R" else n
+    nrows = nc if which in ("R", "M") else n
     ncols = nc if which == "P" else n
-    nnz = info["nnz"][level] if which == "A" else info["nnz_p"][level]
+    nnz = {"A": lambda: info["nnz"][level], "P": lambda: info["nnz_p"][level],
+           "R": lambda: info["nnz_p"][level], "M": lambda: amg_fused_restriction_nnz(h, level)}[which]()
     ptr = np.zeros(nrows + 1, np.int32)
     col = np.zeros(max(nnz, 1), np.int32)
     val = np.zeros(max(nnz, 1), np.float64)

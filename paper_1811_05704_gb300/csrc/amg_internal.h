@@ -60,6 +60,7 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
 // the updates of x, r, p; BiCGStab: two of each and its longer updates.
 struct LevelSizes {
     int64_t n, nnz, nnz_p;
+    int64_t nnz_m = 0;  // nonzeros of the fused restriction operator (0: not used)
 };
 double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver);
 
@@ -185,6 +186,9 @@ void launch_residual(const DevCsr& A, const double* f, const double* x, double* 
 // x += P xc
 void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int* skip,
                         cudaStream_t s);
+// x = d f + P xc (the level's pre-sweep folded into the fused restriction)
+void launch_prolong_pre(const DevCsr& P, const double* d, const double* f, const double* xc, double* x,
+                        const int* skip, cudaStream_t s);
 
 // float32 V-cycle variants (mixed precision)
 void launch_spmv_f32(const DevCsr& A, const float* x, float* y, const int* skip, cudaStream_t s);
@@ -257,6 +261,8 @@ int64_t dev_aggregate(const DevCsr& A, const double* dg, double eps, int32_t* ag
 void dev_prolongation(const DevCsr& A, const double* dg, const uint8_t* strong, const int32_t* agg,
                       int64_t nagg, DevCsr& P, double& omega, cudaStream_t s);
 void dev_transpose(const DevCsr& P, DevCsr& R, cudaStream_t s);
+// M holds R A (from device_spgemm); its values become those of R - (R A) D.
+void dev_fused_restriction(const DevCsr& R, const double* d, DevCsr& M, cudaStream_t s);
 
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.

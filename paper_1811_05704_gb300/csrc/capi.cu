@@ -383,12 +383,22 @@ amg_status amg_hierarchy_info(const amg_handle* h, int* levels, int64_t* rows, i
     });
 }
 
+amg_status amg_fused_restriction_nnz(const amg_handle* h, int level, int64_t* nnz) {
+    return guarded([&]() -> amg_status {
+        const Level& L = level_of(h, level);
+        if (!nnz) fail(AMG_ERR_INVALID_ARG, "null output");
+        *nnz = L.M.nrows > 0 ? L.M.nnz : 0;
+        return AMG_OK;
+    });
+}
+
 amg_status amg_hierarchy_bytes(const amg_handle* h, double* bytes_per_iteration) {
     return guarded([&]() -> amg_status {
         if (!h || !bytes_per_iteration) fail(AMG_ERR_INVALID_ARG, "null argument");
         std::vector<LevelSizes> sz(h->lev.size());
         for (size_t l = 0; l < h->lev.size(); ++l)
-            sz[l] = {h->lev[l].A.nrows, h->lev[l].A.nnz, l + 1 < h->lev.size() ? h->lev[l].P.nnz : 0};
+            sz[l] = {h->lev[l].A.nrows, h->lev[l].A.nnz, l + 1 < h->lev.size() ? h->lev[l].P.nnz : 0,
+                     h->lev[l].M.nrows > 0 ? h->lev[l].M.nnz : 0};
         *bytes_per_iteration = krylov_iteration_bytes(sz, h->prm.precision, h->prm.solver);
         return AMG_OK;
     });
@@ -398,12 +408,13 @@ amg_status amg_get_level_matrix(const amg_handle* h, int level, int which, int32
                                 int32_t* col, double* val) {
     return guarded([&]() -> amg_status {
         const Level& L = level_of(h, level);
-        if (which < 0 || which > 2) fail(AMG_ERR_INVALID_ARG, "which must be 0 (A), 1 (P) or 2 (R)");
+        if (which < 0 || which > 3) fail(AMG_ERR_INVALID_ARG, "which must be 0 (A), 1 (P), 2 (R) or 3 (M)");
         if (which > 0 && level + 1 >= (int)h->lev.size())
-            fail(AMG_ERR_INVALID_ARG, "the coarsest level has no P or R");
+            fail(AMG_ERR_INVALID_ARG, "the coarsest level has no P, R or M");
+        if (which == 3 && L.M.nrows == 0) fail(AMG_ERR_INVALID_ARG, "this level has no fused restriction operator");
         if (!row_ptr || !col || !val) fail(AMG_ERR_INVALID_ARG, "null output");
         AMG_CUDA(cudaSetDevice(h->device));
-        const DevCsr& D = which == 0 ? L.A : which == 1 ? L.P : L.R;
+        const DevCsr& D = which == 0 ? L.A : which == 1 ? L.P : which == 2 ? L.R : L.M;
         AMG_CUDA(cudaMemcpy(row_ptr, D.ptr, (D.nrows + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
         AMG_CUDA(cudaMemcpy(col, D.col, D.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
         AMG_CUDA(cudaMemcpy(val, D.val, D.nnz * sizeof(double), cudaMemcpyDeviceToHost));

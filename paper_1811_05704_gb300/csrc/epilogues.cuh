@@ -239,6 +239,26 @@ struct EpiProlong {  // x += P xc
     __device__ void store(int r, double xs, const Pre&, double&, double&) const { x[r] = xs; }
 };
 
+// x = d f + P xc: the prolongation and correction of a level whose first
+// pre-sweep (x = d f from zero) was folded into the fused restriction
+// operator; the pre-sweep's x is formed here, as the seed of the product.
+struct EpiProlongPre {
+    using acc_t = double;
+    struct Pre { double d, f; };
+    static constexpr int ndot = 0, nvec = 2;
+    const double* __restrict__ d;
+    const double* __restrict__ f;
+    const double* __restrict__ xc;
+    double* __restrict__ x;
+    __device__ const void* vptr(int k) const { return k == 0 ? (const void*)d : (const void*)f; }
+    __device__ int vbytes(int) const { return 8; }
+    __device__ double xg(int c) const { return __ldg(xc + c); }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r), v.at<double>(1, r)}; }
+    static constexpr int kSeed = +1;
+    __device__ double seed(const Pre& p) const { return p.d * p.f; }
+    __device__ void store(int r, double xs, const Pre&, double&, double&) const { x[r] = xs; }
+};
+
 // float32 V-cycle: level vectors and matrix values in float32, float32
 // accumulation; on the finest level the right-hand side (the Krylov vector)
 // is read in float64 and the output written in float64.

@@ -13,6 +13,10 @@ namespace amg {
 
 struct Level {
     DevCsr A, P, R;             // P, R unused on the coarsest level
+    // fused restriction operator M = R (I - A D) (one pre-sweep from zero,
+    // the residual and the restriction as one product), where it moves
+    // fewer bytes than the three steps; M.nrows == 0 if not used
+    DevCsr M;
     double* d = nullptr;        // smoother diagonal
     float* d32 = nullptr;
     // level vectors: f rhs (unused on level 0), x pre-smoothed / corrected

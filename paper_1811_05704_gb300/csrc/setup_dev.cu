@@ -239,6 +239,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_long_rows(const int32_t* 
     }
 }
 
+// Raises the long-row kernels' shared-memory limit (defined below them).
+void allow_sort_smem();
+
 void dev_sort_rows(int64_t n, const int32_t* ptr, int32_t* key, int32_t* pay, cudaStream_t s) {
     if (n == 0) return;
     Tmp t(s);
@@ -270,7 +273,7 @@ void dev_sort_rows(int64_t n, const int32_t* ptr, int32_t* key, int32_t* pay, cu
         scratch = t.get<unsigned long long>((size_t)grid * m);
     }
     const size_t smem = (size_t)std::min(m, kSmemSort) * sizeof(unsigned long long);
-    AMG_CUDA(cudaFuncSetAttribute(k_sort_long_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_sort_smem();
     k_sort_long_rows<<<grid, kSortThreads, smem, s>>>(rows, hl, ptr, key, pay, scratch, scratch_len);
     AMG_CUDA(cudaGetLastError());
 }
@@ -799,10 +802,49 @@ __global__ void __launch_bounds__(kSortThreads) k_prolong_long(
     }
 }
 
+// The long-row kernels' shared-memory limit is raised once, to the largest
+// size any launch asks for: set-ups on several host threads at once (the
+// server) must not change a kernel's attribute between another thread's
+// setting and its launch.
+void allow_sort_smem() {
+    static const bool done = [] {
+        const int bytes = kSmemSort * (int)sizeof(unsigned long long);
+        AMG_CUDA(cudaFuncSetAttribute(k_sort_long_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        AMG_CUDA(cudaFuncSetAttribute(k_prolong_long<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        AMG_CUDA(cudaFuncSetAttribute(k_prolong_long<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        return true;
+    }();
+    (void)done;
+}
+
 __global__ void __launch_bounds__(kT) k_gather_vals(int64_t nnz, const int32_t* __restrict__ perm,
                                                     const double* __restrict__ src, double* __restrict__ dst) {
     const int64_t q = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (q < nnz) dst[q] = src[perm[q]];
+}
+
+
+// ---------------------------------------------- fused restriction operator
+// M = R - (R A) D on the pattern of R A (which contains R's: A has its
+// diagonal): row c of M merges row c of R into row c of R A.
+__global__ void __launch_bounds__(kT) k_fused_restriction(int64_t m, const int32_t* __restrict__ rptr,
+                                                          const int32_t* __restrict__ rcol,
+                                                          const double* __restrict__ rval,
+                                                          const int32_t* __restrict__ mptr,
+                                                          const int32_t* __restrict__ mcol,
+                                                          double* __restrict__ mval, const double* __restrict__ d,
+                                                          int* __restrict__ err) {
+    const int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (c >= m) return;
+    int q = rptr[c];
+    const int qe = rptr[c + 1];
+    for (int k = mptr[c]; k < mptr[c + 1]; ++k) {
+        const int j = mcol[k];
+        double r = 0.0;
+        if (q < qe && rcol[q] == j) r = rval[q++];
+        mval[k] = __dsub_rn(r, __dmul_rn(mval[k], d[j]));
+    }
+    if (q != qe) atomicOr(err, 1);  // an entry of R outside the pattern of R A: cannot happen
 }
 
 }  // namespace
@@ -941,8 +983,7 @@ void dev_prolongation(const DevCsr& A, const double* dg, const uint8_t* strong, 
         grid = std::min(hl, 2 * sms);
         if (m > kSmemSort) scratch = t.get<unsigned long long>((size_t)grid * m);
         smem = (size_t)std::min(m, kSmemSort) * sizeof(unsigned long long);
-        AMG_CUDA(cudaFuncSetAttribute(k_prolong_long<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        AMG_CUDA(cudaFuncSetAttribute(k_prolong_long<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_sort_smem();
         k_prolong_long<false><<<grid, kSortThreads, smem, s>>>(long_rows, hl, A.ptr, A.col, A.val, strong, agg, tv,
                                                                dF, om, count, nullptr, nullptr, nullptr, scratch,
                                                                m > kSmemSort ? m : 0);
@@ -985,6 +1026,15 @@ void dev_transpose(const DevCsr& P, DevCsr& R, cudaStream_t s) {
     if (R.nnz > 0) k_gather_vals<<<grid_for(R.nnz), kT, 0, s>>>(R.nnz, T.perm, P.val, R.val);
     AMG_CUDA(cudaGetLastError());
     AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+void dev_fused_restriction(const DevCsr& R, const double* d, DevCsr& M, cudaStream_t s) {
+    Tmp t(s);
+    int* err = t.get<int>(1);
+    AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_fused_restriction<<<grid_for(M.nrows), kT, 0, s>>>(M.nrows, R.ptr, R.col, R.val, M.ptr, M.col, M.val, d, err);
+    AMG_CUDA(cudaGetLastError());
+    if (read1(err, s)) fail(AMG_ERR_CUDA, "fused restriction: R outside the pattern of R A");
 }
 
 }  // namespace amg

@@ -470,11 +470,16 @@ double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision,
     double vc = 0.0;  // one V-cycle
     for (size_t l = 0; l + 1 < L; ++l) {
         const double n = (double)lev[l].n, z = (double)lev[l].nnz, zp = (double)lev[l].nnz_p;
-        const double nc = (double)lev[l + 1].n;
-        vc += e * z + 4 * n + 4 * v * n;             // pre-sweep + residual: d, f read; x, t written
-        vc += e * zp + 4 * nc + v * n + v * nc;      // restriction: t gathered, f_{l+1} written
-        vc += e * zp + 4 * n + v * nc + 2 * v * n;   // prolongation + correction
-        vc += e * z + 4 * n + 4 * v * n;             // post-sweep: x gathered, d, f read, y written
+        const double nc = (double)lev[l + 1].n, zm = (double)lev[l].nnz_m;
+        if (zm > 0) {
+            vc += e * zm + 4 * nc + v * n + v * nc;      // f_{l+1} = M f: f gathered, f_{l+1} written
+            vc += e * zp + 4 * n + v * nc + 3 * v * n;   // x = d f + P x_{l+1}: d, f read, x written
+        } else {
+            vc += e * z + 4 * n + 4 * v * n;             // pre-sweep + residual: d, f read; x, t written
+            vc += e * zp + 4 * nc + v * n + v * nc;      // restriction: t gathered, f_{l+1} written
+            vc += e * zp + 4 * n + v * nc + 2 * v * n;   // prolongation + correction
+        }
+        vc += e * z + 4 * n + 4 * v * n;                 // post-sweep: x gathered, d, f read, y written
     }
     const double nL = (double)lev[L - 1].n;
     vc += 8 * nL * nL + 2 * v * nL;                  // dense coarsest solve (float64 inverse)

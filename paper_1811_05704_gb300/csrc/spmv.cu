@@ -647,6 +647,10 @@ void launch_prolong_add(const DevCsr& P, const double* xc, double* x, const int*
                         cudaStream_t s) {
     run(P, P.val, EpiProlong{xc, x}, Reduce{}, skip, s);
 }
+void launch_prolong_pre(const DevCsr& P, const double* d, const double* f, const double* xc, double* x,
+                        const int* skip, cudaStream_t s) {
+    run(P, P.val, EpiProlongPre{d, f, xc, x}, Reduce{}, skip, s);
+}
 
 static const __nv_bfloat16* bf16_of(const uint16_t* p) { return reinterpret_cast<const __nv_bfloat16*>(p); }
 

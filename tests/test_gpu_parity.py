@@ -158,6 +158,41 @@ def test_hierarchy_bit_exact(amg, case, device_setup):
     S.close()
 
 
+@pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18", "spai0_varcoef"])
+def test_fused_restriction_operator(amg, case):
+    """Where a level uses the fused restriction operator, M = R - R A D
+    (D the smoother diagonal), entry by entry against scipy's sparse products of
+    the level's own R, A and d, on the structural pattern of R A.  The finest
+    level of the 7-point problems uses it."""
+    make, kw = CASES[case]
+    A = make()
+    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, **kw)
+    info = S.info()
+    used = 0
+    for l in range(info["levels"] - 1):
+        if amg.amg_fused_restriction_nnz(S.handle, l) == 0:
+            continue
+        used += 1
+        import scipy.sparse as sp
+        mats = {}
+        for w in "ARM":
+            ptr, col, val, shape = amg.amg_get_level_matrix(S.handle, l, w)
+            mats[w] = sp.csr_matrix((val, col, ptr), shape=shape)
+            # structural pattern, stored zeros included
+            mats[w + "s"] = sp.csr_matrix((np.ones(len(col)), col, ptr), shape=shape)
+        dl = amg.amg_get_smoother_diag(S.handle, l)
+        ref = mats["R"] - (mats["R"] @ mats["A"]) @ sp.diags(dl)
+        diff = (mats["M"] - ref).tocsr()
+        assert abs(diff).max() <= 1e-14 * abs(ref).max(), l
+        pat = (mats["Rs"] @ mats["As"]).tocsr()
+        pat.sort_indices()
+        assert np.array_equal(pat.indptr, mats["Ms"].indptr), l
+        assert np.array_equal(pat.indices, mats["Ms"].indices), l
+    if case == "poisson32":
+        assert amg.amg_fused_restriction_nnz(S.handle, 0) > 0
+    S.close()
+
+
 def _row_bound(ptr, col, val, x):
     rows = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
     return np.bincount(rows, weights=np.abs(val * x[col]), minlength=len(ptr) - 1)

@@ -81,3 +81,59 @@ def test_noalloc_refuses_matrix_above_its_limit(amg):
     # the allocating entry point handles the same matrix
     amg.amg_spmv_dot(amg.make_csr(n, rp, cl, vl), x, y, d)
     assert d.item() == 2.0 * n
+
+
+def _cudart():
+    """The CUDA runtime as a shared library (the toolkit's), for reading the
+    device's default memory pool, from which amg_spmv_dot's stream-ordered
+    scratch comes."""
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.fail("no CUDA runtime shared library found")
+
+
+# cudaMemPoolAttr values of the CUDA runtime API
+_RESERVED_CURRENT, _USED_CURRENT, _USED_HIGH = 5, 7, 8
+
+
+def test_noalloc_moves_no_pool_watermark(amg):
+    """The reason for the entry point: it allocates nothing.  After a first
+    (warm-up) call, the device's default memory pool -- where amg_spmv_dot's
+    scratch comes from -- keeps its used-memory high watermark and its
+    reserved size through two more calls; one amg_spmv_dot call then raises
+    the watermark, which shows that the check sees an allocation."""
+    import ctypes
+    import torch
+    dev = torch.device("cuda:0")
+    rt = _cudart()
+    A = gen.poisson3d(40)
+    rp, cl, vl = (torch.from_numpy(a).to(dev) for a in (A.row_ptr, A.col, A.val))
+    csr = amg.make_csr(A.n, rp, cl, vl)
+    x = torch.from_numpy(gen.uniform_pm1(3, 30, A.n)).to(dev)
+    y = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    amg.amg_spmv_dot_noalloc(csr, x, y, d)
+    torch.cuda.synchronize()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), 0) == 0
+
+    def attr(a):
+        v = ctypes.c_uint64()
+        assert rt.cudaMemPoolGetAttribute(pool, a, ctypes.byref(v)) == 0
+        return v.value
+
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, _USED_HIGH, ctypes.byref(zero)) == 0
+    used0, reserved0 = attr(_USED_CURRENT), attr(_RESERVED_CURRENT)
+    for _ in range(2):
+        amg.amg_spmv_dot_noalloc(csr, x, y, d)
+    torch.cuda.synchronize()
+    assert attr(_USED_HIGH) <= used0
+    assert attr(_RESERVED_CURRENT) == reserved0
+    amg.amg_spmv_dot(csr, x, y, d)
+    torch.cuda.synchronize()
+    assert attr(_USED_HIGH) > used0
