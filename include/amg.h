@@ -182,7 +182,8 @@ amg_status amg_get_level_matrix(const amg_handle *h, int level, int which, int32
  * is R (f - A D f) = M f, M = R - R A D, D = diag(d).  The set-up forms M
  * where one product with it moves fewer bytes than the three steps, and the
  * V-cycle then computes f_{l+1} = M f going down and x = d f + P x_{l+1}
- * coming up.  Only for the float64 V-cycle, with npre = 1 and use_tail = 0.) */
+ * coming up.  With npre = 1 and use_tail = 0; the float32 V-cycle uses it on
+ * levels >= 1 only, the bfloat16-stored one not at all.) */
 amg_status amg_fused_restriction_nnz(const amg_handle *h, int level, int64_t *nnz);
 
 /* Aggregate id of every row of level l (host array of rows[l] entries);

@@ -200,6 +200,8 @@ void launch_smooth_f32(const DevCsr& A, const float* d, const float* f32, const 
                        const Reduce* r, const int* skip, cudaStream_t s);
 void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const int* skip,
                             cudaStream_t s);
+void launch_prolong_pre_f32(const DevCsr& P, const float* d, const float* f, const float* xc, float* x,
+                            const int* skip, cudaStream_t s);
 
 // vector kernels
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s);

@@ -354,6 +354,22 @@ struct EpiSmooth32 {
     }
 };
 
+struct EpiProlongPre32 {  // as EpiProlongPre, float32 vectors
+    using acc_t = float;
+    struct Pre { float d, f; };
+    static constexpr int ndot = 0, nvec = 2;
+    const float* __restrict__ d;
+    const float* __restrict__ f;
+    const float* __restrict__ xc;
+    float* __restrict__ x;
+    __device__ const void* vptr(int k) const { return k == 0 ? (const void*)d : (const void*)f; }
+    __device__ int vbytes(int) const { return 4; }
+    __host__ __device__ static constexpr int vslot(int) { return 4; }
+    __device__ float xg(int c) const { return __ldg(xc + c); }
+    __device__ Pre load(int r, const VecTile& v) const { return {v.at<float>(0, r), v.at<float>(1, r)}; }
+    __device__ void store(int r, float s, const Pre& p, double&, double&) const { x[r] = p.d * p.f + s; }
+};
+
 struct EpiProlong32 {
     using acc_t = float;
     struct Pre { float x; };

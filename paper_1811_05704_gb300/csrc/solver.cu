@@ -180,19 +180,26 @@ static std::vector<int32_t> download_ptr(const DevCsr& D, cudaStream_t s) {
 // (x = d f + P x_{l+1}).  M replaces the pre-sweep's product, the round trip
 // of t and the product with R by one product, where that moves fewer bytes:
 // nnz(M) < nnz(A) + nnz(P) + 7n/3 (12 bytes per nonzero against the 28 bytes
-// per row that the separate steps move in addition).  R A is formed only if
-// its size bound sum_i nnz(A_i) nnz(P_i) makes that plausible.
-static void build_fused_restriction(amg_handle* h, Level& L, const std::vector<int32_t>& aptr,
+// per row that the separate steps move in addition).  R A is formed only
+// when its size bound sum_i nnz(A_i) nnz(P_i) is at most 12 times that and
+// at most 2^28 (the rows of R overlap heavily on coarse levels, so the bound
+// overestimates nnz(R A) 2-13 times on 3D stencils; the cap keeps the dense
+// coarse levels of strongly varying coefficients from costing a huge
+// product).  The float32 V-cycle keeps the separate steps on the finest
+// level, where M's longer rows cost their gathers more than M saves, and the
+// bfloat16-stored one everywhere (no gain there, and M's entries rounded to
+// bfloat16 cost an iteration); both measured on 150^3 Poisson.
+static void build_fused_restriction(amg_handle* h, Level& L, int level, const std::vector<int32_t>& aptr,
                                     const std::vector<int32_t>& pptr) {
-    // measured on 150^3 Poisson: 1.4% faster in float64; the float32 and
-    // bfloat16 V-cycles, which are not bound by a pipe, lost 1.5% and 3% with it
-    if (h->prm.npre != 1 || h->prm.use_tail || h->prm.precision != AMG_PRECISION_FP64) return;
+    const bool f32 = h->prm.precision != AMG_PRECISION_FP64;
+    if (h->prm.npre != 1 || h->prm.use_tail || (f32 && level == 0) || h->prm.precision == AMG_PRECISION_BF16)
+        return;
     const int64_t n = L.A.nrows;
     double bound = 0.0;
     for (int64_t i = 0; i < n; ++i)
         bound += (double)(aptr[i + 1] - aptr[i]) * (double)(pptr[i + 1] - pptr[i]);
     const double keep = (double)L.A.nnz + (double)L.P.nnz + 7.0 * (double)n / 3.0;
-    if (bound > 3.0 * keep) return;
+    if (bound > 12.0 * keep || bound > (double)(1 << 28)) return;
     DevCsr M;
     device_spgemm(L.R, L.A, M, h->stream);
     if ((double)M.nnz >= keep) {
@@ -204,6 +211,7 @@ static void build_fused_restriction(amg_handle* h, Level& L, const std::vector<i
     track(h, M);
     dev_fused_restriction(L.R, L.d, M, h->stream);
     schedule(h, download_ptr(M, h->stream), M, kRowsPerBlock);
+    if (f32) make_f32(h, M);
     L.M = M;
 }
 
@@ -303,7 +311,7 @@ static void build_hierarchy_dev(amg_handle* h, const HostCsr& A0) {
                     std::vector<int32_t> cptr = download_ptr(Ac, s);
                     schedule(h, cptr, Ac, kRowsPerBlock);
                     if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
-                    build_fused_restriction(h, L, aptr, pptr);
+                    build_fused_restriction(h, L, l, aptr, pptr);
                     aptr = std::move(cptr);
                     h->lev.emplace_back();
                     h->lev.back().A = Ac;
@@ -405,7 +413,7 @@ void build_hierarchy(amg_handle* h, HostCsr A) {
                 download(Ac, next, h->stream);
                 schedule(h, next.ptr, Ac, kRowsPerBlock);
                 if (f32) { make_f32(h, L.P); make_f32(h, L.R); }
-                build_fused_restriction(h, L, A.ptr, P.ptr);
+                build_fused_restriction(h, L, l, A.ptr, P.ptr);
                 h->lev.emplace_back();
                 h->lev.back().A = Ac;
                 A = std::move(next);
@@ -601,6 +609,10 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, const float
         Level& v = L[l];
         const int kcp = l == 0 ? AMG_KC_PRESMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
         const int kcr = l == 0 ? AMG_KC_RESTRICT_L0 : AMG_KC_VCYCLE_COARSER;
+        if (v.M.nrows > 0) {  // f_{l+1} = M f (pre-sweep, residual and restriction; levels >= 1)
+            I.pre(kcr); launch_spmv_f32(v.M, v.f32, L[l + 1].f32, skip, s); I.post();
+            continue;
+        }
         I.pre(kcp);
         launch_presmooth_residual_f32(v.A, v.d32, l == 0 ? r32 : v.f32, (l == 0 && !r32) ? r : nullptr,
                                       v.x32, v.t32, skip, s);
@@ -620,7 +632,11 @@ static void issue_vcycle32(amg_handle* h, Issue& I, const double* r, const float
         Level& v = L[l];
         const int kc = l == 0 ? AMG_KC_PROLONG_L0 : AMG_KC_VCYCLE_COARSER;
         const int kcs = l == 0 ? AMG_KC_POSTSMOOTH_L0 : AMG_KC_VCYCLE_COARSER;
-        I.pre(kc); launch_prolong_add_f32(v.P, below, v.x32, skip, s); I.post();
+        if (v.M.nrows > 0) {  // x = d f + P x_{l+1}
+            I.pre(kc); launch_prolong_pre_f32(v.P, v.d32, v.f32, below, v.x32, skip, s); I.post();
+        } else {
+            I.pre(kc); launch_prolong_add_f32(v.P, below, v.x32, skip, s); I.post();
+        }
         I.pre(kcs);
         launch_smooth_f32(v.A, v.d32, l == 0 ? r32 : v.f32, (l == 0 && !r32) ? r : nullptr, v.x32,
                           l == 0 ? nullptr : v.y32, l == 0 ? z : nullptr,

@@ -703,6 +703,11 @@ void launch_prolong_add_f32(const DevCsr& P, const float* xc, float* x, const in
     run32(P, P.val32, P.val16, EpiProlong32{xc, x}, Reduce{}, skip, s);
 }
 
+void launch_prolong_pre_f32(const DevCsr& P, const float* d, const float* f, const float* xc, float* x,
+                            const int* skip, cudaStream_t s) {
+    run32(P, P.val32, P.val16, EpiProlongPre32{d, f, xc, x}, Reduce{}, skip, s);
+}
+
 // Standalone product on a caller's device CSR: uniform row split (no
 // schedule to build), column indices bounds-checked (a bad index sets bit 1
 // of *err and contributes zero).
