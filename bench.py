@@ -8,6 +8,13 @@ FP64.  A step is one complete solve on the resident hierarchy (setup excluded,
 as in the metric).  The finest-level matrix alone (282 MB) exceeds the 129 MB
 L2, so no L2 flush is needed between steps.
 
+The same JSON line carries the other workloads as legs: the float32 and
+bfloat16-stored V-cycles on the same problem (`mixed`), the 200^3
+variable-coefficient problem in three precisions (`varcoef200`), 4096 batched
+2D systems in one persistent launch (`batched`) and a stream of 2000 served
+requests (`serving`); each leg can be skipped (--no-mixed, --no-varcoef,
+--no-batch, --no-serve).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
@@ -513,9 +520,12 @@ def bench_serving(amg, args, rank=0, world=1, dev=None):
     mats = _serve_matrices(reqs)
     gen_s = time.perf_counter() - t0
     A_of = lambda q: mats[(q.kind, q.side)]  # noqa: E731
-    # CG + damped Jacobi for SPD requests; BiCGStab + SPAI-0 for convection-diffusion
-    prm_cg = amg.amg_params_default()
-    prm_bi = amg.amg_params_default(solver=amg.AMG_SOLVER_BICGSTAB, smoother=amg.AMG_SMOOTHER_SPAI0)
+    # CG + damped Jacobi for SPD requests; BiCGStab + SPAI-0 for convection-diffusion.  Most
+    # requests get one solve per set-up, so the fused restriction operator (a set-up product
+    # that pays off over several solves) is left out, for the server and the plain API alike.
+    prm_cg = amg.amg_params_default(fused_restriction=0)
+    prm_bi = amg.amg_params_default(solver=amg.AMG_SOLVER_BICGSTAB, smoother=amg.AMG_SMOOTHER_SPAI0,
+                                    fused_restriction=0)
     prm_of = lambda q: prm_bi if q.solver else prm_cg  # noqa: E731
     rhs = {q.index: q.rhs(SEED, A_of(q).n) for q in reqs}
     csrs = {c: amg.make_csr(A.n, A.row_ptr, A.col, A.val) for c, A in mats.items()}

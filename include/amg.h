@@ -97,6 +97,12 @@ typedef struct {
                               device; 0 = the graph steps on host threads (the Galerkin
                               product stays on the GPU).  Both give the same hierarchy, bit
                               for bit. */
+    int fused_restriction; /* [1] form the fused restriction operator M = R - R A D on the
+                              levels where one product with it moves fewer bytes than the
+                              pre-sweep, residual and restriction (amg_fused_restriction_nnz);
+                              it costs a sparse product per level at set-up and pays off over
+                              a few solves, so callers that solve once per hierarchy may turn
+                              it off.  Results agree to rounding either way. */
 } amg_params;
 
 /* A CSR matrix as passed in by the caller (see the conventions above). */

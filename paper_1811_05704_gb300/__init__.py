@@ -52,6 +52,7 @@ class amg_params(C.Structure):
         ("use_pdl", C.c_int),
         ("use_tail", C.c_int),
         ("device_setup", C.c_int),
+        ("fused_restriction", C.c_int),
     ]
 
 

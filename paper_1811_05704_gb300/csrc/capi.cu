@@ -191,6 +191,7 @@ amg_status amg_params_default(amg_params* p) {
     p->use_pdl = 1;
     p->use_tail = 0;
     p->device_setup = 1;
+    p->fused_restriction = 1;
     return AMG_OK;
 }
 

@@ -192,7 +192,8 @@ static std::vector<int32_t> download_ptr(const DevCsr& D, cudaStream_t s) {
 static void build_fused_restriction(amg_handle* h, Level& L, int level, const std::vector<int32_t>& aptr,
                                     const std::vector<int32_t>& pptr) {
     const bool f32 = h->prm.precision != AMG_PRECISION_FP64;
-    if (h->prm.npre != 1 || h->prm.use_tail || (f32 && level == 0) || h->prm.precision == AMG_PRECISION_BF16)
+    if (!h->prm.fused_restriction || h->prm.npre != 1 || h->prm.use_tail || (f32 && level == 0) ||
+        h->prm.precision == AMG_PRECISION_BF16)
         return;
     const int64_t n = L.A.nrows;
     double bound = 0.0;
