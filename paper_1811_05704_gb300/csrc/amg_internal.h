@@ -266,6 +266,10 @@ void dev_transpose(const DevCsr& P, DevCsr& R, cudaStream_t s);
 // M holds R A (from device_spgemm); its values become those of R - (R A) D.
 void dev_fused_restriction(const DevCsr& R, const double* d, DevCsr& M, cudaStream_t s);
 
+// out[0..n] = exclusive prefix sums of in[0..n-1] (setup_dev.cu); returns the
+// total; fails with TOO_LARGE if it reaches 2^31 - 1.
+int64_t dev_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+
 // Galerkin product on the device (spgemm.cu): C = A B, pattern structural,
 // entries accumulated in ascending order of the inner index.
 // C's arrays are stream-ordered allocations on s (free with dev_free_async).

@@ -31,7 +31,10 @@ inline unsigned host_threads() {
 }
 
 // Run fn(i) for i in [0, n) on host_threads() threads; rethrows the first
-// exception after all workers finished.
+// exception after all workers finished.  Parallel steps inside fn run on the
+// calling worker alone (the workers' thread cap is 1), so nested parallelism
+// -- the per-system set-ups of the batched form -- does not oversubscribe the
+// host.
 template <class F>
 void parallel_for(int64_t n, F&& fn) {
     const unsigned nt = (unsigned)std::min<int64_t>(host_threads(), std::max<int64_t>(n, 1));
@@ -39,6 +42,8 @@ void parallel_for(int64_t n, F&& fn) {
     std::exception_ptr err;
     std::mutex m;
     auto worker = [&]() {
+        const unsigned saved = t_thread_cap;
+        if (nt > 1) t_thread_cap = 1;
         for (;;) {
             const int64_t i = next++;
             if (i >= n) break;
@@ -49,6 +54,7 @@ void parallel_for(int64_t n, F&& fn) {
                 if (!err) err = std::current_exception();
             }
         }
+        t_thread_cap = saved;
     };
     std::vector<std::thread> pool;
     for (unsigned t = 1; t < nt; ++t) pool.emplace_back(worker);

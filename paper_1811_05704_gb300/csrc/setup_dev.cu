@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kT) k_scan_apply(int64_t n, const int32_t* __r
     if (blockIdx.x == nb - 1 && threadIdx.x == kT - 1) out[n] = (int32_t)tot[nb];
 }
 
+}  // namespace
+
 // out[0..n] = exclusive prefix of in[0..n-1]; returns out[n] (the total).
 int64_t dev_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
     Tmp t(s);
@@ -157,9 +159,11 @@ int64_t dev_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStrea
     k_scan_block_totals<<<1, 1024, 0, s>>>(nb, tot, overflow);
     k_scan_apply<<<nb, kT, 0, s>>>(n, in, tot, nb, out);
     AMG_CUDA(cudaGetLastError());
-    if (read1(overflow, s)) fail(AMG_ERR_TOO_LARGE, "set-up array with more than 2^31 entries");
+    if (read1(overflow, s)) fail(AMG_ERR_TOO_LARGE, "set-up array (or Galerkin product) with more than 2^31 entries");
     return read1(out + n, s);
 }
+
+namespace {
 
 // ------------------------------------------------------ segmented sorting
 // Rows of a CSR-like array sorted by key, carrying a payload.  Rows of up to
@@ -409,6 +413,7 @@ __global__ void __launch_bounds__(kT) k_strength(int64_t n, const int32_t* __res
 
 // ------------------------------------------------------------ aggregation
 constexpr int kUndecided = 0, kRoot = 1, kOut = 2;  // pass-1 / pass-3 node states
+constexpr int kRes = 8;                              // pass 1: resources checked together
 constexpr int kNotFree = 3;                          // pass 3: aggregated before pass 3
 
 __device__ __forceinline__ int ld_relaxed(const int* p) {
@@ -467,31 +472,63 @@ __global__ void __launch_bounds__(kT) k_pass1(int n, const int32_t* __restrict__
         const int i = base + lane;
         if (i < n && ld_relaxed(state + i) == kUndecided) {
             const unsigned long long t0 = now_ns();
+            const int kb = ptr[i], ke = ptr[i + 1];
+            // resources before kpos are known to be clear for i (their
+            // cursors reached i, and cannot pass it before i decides): a
+            // retry starts at the first one that was not
+            int kpos = kb - 1;
             for (unsigned spin = 0;; ++spin) {
                 bool blocked = false, out = false;
-                for (int k = ptr[i] - 1; k < ptr[i + 1] && !out; ++k) {
-                    int j;
-                    if (k < ptr[i]) j = i;
-                    else if (strong[k]) j = col[k];
-                    else continue;
-                    const int tb = tptr[j], len = tptr[j + 1] - tb;
-                    const int c0 = ld_relaxed(cursor + j);
-                    int c = c0;
-                    for (;;) {
-                        if (c >= len) {  // i is in every candidate list it walks: cannot happen
-                            atomicOr(err, 1);
-                            out = true;
+                // resources in batches of kRes: their list heads, cursors,
+                // candidates and states are loaded together (independent
+                // loads), then each resource is resolved, walking further
+                // only past candidates that did not seed
+                for (int k0 = kpos; k0 < ke && !out; k0 += kRes) {
+                    int jj[kRes], tb[kRes], len[kRes], c0[kRes], rr[kRes], st[kRes];
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u) {
+                        const int k = k0 + u;
+                        jj[u] = (k < kb) ? i : (k < ke && strong[k]) ? col[k] : -1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u) {
+                        tb[u] = len[u] = c0[u] = 0;
+                        if (jj[u] >= 0) {
+                            tb[u] = tptr[jj[u]];
+                            len[u] = tptr[jj[u] + 1] - tb[u];
+                            c0[u] = ld_relaxed(cursor + jj[u]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u)
+                        rr[u] = (jj[u] >= 0 && c0[u] < len[u]) ? tcol[tb[u] + c0[u]] : i;
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u) st[u] = (rr[u] < i) ? ld_relaxed(state + rr[u]) : kUndecided;
+                    for (int u = 0; u < kRes && !out; ++u) {
+                        if (jj[u] < 0) continue;
+                        int c = c0[u], r = rr[u], sr = st[u];
+                        for (;;) {
+                            if (c >= len[u]) {  // i is in every candidate list it walks: cannot happen
+                                atomicOr(err, 1);
+                                out = true;
+                                break;
+                            }
+                            if (r >= i) break;
+                            if (sr == kOut) {
+                                ++c;
+                                if (c < len[u]) {
+                                    r = tcol[tb[u] + c];
+                                    sr = (r < i) ? ld_relaxed(state + r) : kUndecided;
+                                }
+                                continue;
+                            }
+                            if (sr == kRoot) out = true;
+                            else blocked = true;
                             break;
                         }
-                        const int r = tcol[tb + c];
-                        if (r >= i) break;
-                        const int st = ld_relaxed(state + r);
-                        if (st == kOut) { ++c; continue; }
-                        if (st == kRoot) out = true;
-                        else blocked = true;
-                        break;
+                        if (c > c0[u]) atomicMax(cursor + jj[u], c);
+                        if (!blocked && !out) kpos = k0 + u + 1;
                     }
-                    if (c > c0) atomicMax(cursor + j, c);
                 }
                 if (out) { st_relaxed(state + i, kOut); break; }
                 if (!blocked) { st_relaxed(state + i, kRoot); break; }
@@ -641,21 +678,28 @@ __global__ void __launch_bounds__(kT) k_filtered(int64_t n, const int32_t* __res
                                                  double* __restrict__ t, double* __restrict__ dF,
                                                  unsigned long long* __restrict__ rho_bits) {
     const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
-    if (i >= n) return;
-    t[i] = __ddiv_rn(1.0, __dsqrt_rn((double)size[agg[i]]));
-    double weak = 0.0;
-    for (int k = ptr[i]; k < ptr[i + 1]; ++k)
-        if (col[k] != i && !strong[k]) weak = __dadd_rn(weak, val[k]);
-    const double f = __dsub_rn(dg[i], weak);
-    dF[i] = f;
-    double row = 0.0;
-    for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
-        if (col[k] == i) row = __dadd_rn(row, fabs(f));
-        else if (strong[k]) row = __dadd_rn(row, fabs(val[k]));
+    // non-negative doubles order like their bit patterns: the maximum is taken
+    // on those, per warp by shuffles, then one atomic per warp
+    unsigned long long bits = 0ull;
+    if (i < n) {
+        t[i] = __ddiv_rn(1.0, __dsqrt_rn((double)size[agg[i]]));
+        double weak = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] != i && !strong[k]) weak = __dadd_rn(weak, val[k]);
+        const double f = __dsub_rn(dg[i], weak);
+        dF[i] = f;
+        double row = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            if (col[k] == i) row = __dadd_rn(row, fabs(f));
+            else if (strong[k]) row = __dadd_rn(row, fabs(val[k]));
+        }
+        bits = (unsigned long long)__double_as_longlong(__ddiv_rn(row, fabs(f)));
     }
-    const double ratio = __ddiv_rn(row, fabs(f));
-    // non-negative doubles order like their bit patterns
-    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = b > bits ? b : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(rho_bits, bits);
 }
 
 __global__ void k_omega(const unsigned long long* __restrict__ rho_bits, double* __restrict__ omega) {
@@ -665,7 +709,7 @@ __global__ void k_omega(const unsigned long long* __restrict__ rho_bits, double*
 // Short rows (at most kShortP nonzeros of A): one thread per row collects the
 // coarse columns in first-seen order with their sums s_ij (each formed in
 // column order), then sorts them by column.  FILL = false counts them only.
-constexpr int kShortP = 32;
+constexpr int kShortP = 96;
 
 template <bool FILL>
 __global__ void __launch_bounds__(kT) k_prolong_short(int64_t n, const int32_t* __restrict__ ptr,

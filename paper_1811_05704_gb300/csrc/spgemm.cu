@@ -33,6 +33,8 @@ constexpr int kBlockSlots = 8192;  // per block; used while distinct <= 4096
 constexpr int kBlockCap = kBlockSlots / 2;
 constexpr int kBlockThreads = 512;
 constexpr int kWarpsPerBlock = 4;
+constexpr int kSmallSlots = 128;   // small-row instances: per warp, used while distinct <= 64
+constexpr int kSmallCap = kSmallSlots / 2;
 constexpr int kEmpty = -1;
 
 __device__ __forceinline__ unsigned slot_of(int key, unsigned mask) {
@@ -54,20 +56,47 @@ __device__ __forceinline__ int insert(int* keys, unsigned mask, int key, bool& a
     return -1;
 }
 
-// error bits: 1 = table overflow (probe failed), 4 = nnz overflow
+// error bit 1: table overflow (probe failed) or symbolic and numeric disagree
 
 // ------------------------------------------------------------- symbolic
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// A warp per row.  Two instances: SMALL (128-slot tables, 8 warps a block)
+// takes the rows whose bound on distinct columns (the sum of the lengths of
+// the rows of B they touch) is at most 64 -- nearly every row of the finest
+// levels -- with many warps resident per SM; the large one (1024-slot
+// tables) takes the others.
+// The large instance runs over the list of rows the small one passed on
+// (`lst`, *nlst entries, a warp each), and lists the rows it finds to have
+// more than kSmallCap distinct columns for the large numeric instance
+// (`mid`, *nmid).
+template <bool SMALL>
+__global__ void __launch_bounds__((SMALL ? 8 : kWarpsPerBlock) * 32)
 k_sym_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict__ ac,
            const int32_t* __restrict__ bp, const int32_t* __restrict__ bc,
            int32_t* __restrict__ count, int32_t* __restrict__ big, int32_t* __restrict__ nbig,
-           int* __restrict__ err) {
-    __shared__ int keys[kWarpsPerBlock][kWarpSlots];
+           int32_t* __restrict__ lst, int32_t* __restrict__ nlst, int32_t* __restrict__ mid,
+           int32_t* __restrict__ nmid, int* __restrict__ err) {
+    constexpr int WARPS = SMALL ? 8 : kWarpsPerBlock;
+    constexpr int SLOTS = SMALL ? kSmallSlots : kWarpSlots;
+    constexpr int CAP = SMALL ? kSmallCap : kWarpCap;
+    __shared__ int keys[WARPS][SLOTS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kWarpsPerBlock + warp;
-    if (row >= m) return;
     int* tab = keys[warp];
-    for (int i = lane; i < kWarpSlots; i += 32) tab[i] = kEmpty;
+    const int nrows = SMALL ? m : *nlst;
+    for (int w = blockIdx.x * WARPS + warp; w < nrows; w += (SMALL ? nrows : gridDim.x * WARPS)) {
+    const int row = SMALL ? w : lst[w];
+    // the row has at most `bound` distinct columns: a table of twice that
+    // (at least 32 slots) is all that has to be cleared
+    int bound = 0;
+    for (int ka = ap[row] + lane; ka < ap[row + 1]; ka += 32) bound += bp[ac[ka] + 1] - bp[ac[ka]];
+    for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
+    if (SMALL && bound > kSmallCap) {  // for the large instance
+        if (lane == 0) lst[atomicAdd(nlst, 1)] = row;
+        continue;
+    }
+    int slots = 32;
+    while (slots < SLOTS && slots < 2 * bound) slots <<= 1;
+    const unsigned mask = (unsigned)slots - 1u;
+    for (int i = lane; i < slots; i += 32) tab[i] = kEmpty;
     __syncwarp();
     int distinct = 0;
     bool overflow = false;
@@ -77,11 +106,11 @@ k_sym_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
         for (int kb = b0; kb < b1; kb += 32) {
             bool added = false;
             if (kb + lane < b1) {
-                if (insert(tab, kWarpSlots - 1, bc[kb + lane], added) < 0) atomicOr(err, 1);
+                if (insert(tab, mask, bc[kb + lane], added) < 0) atomicOr(err, 1);
             }
             distinct += __popc(__ballot_sync(0xffffffffu, added));
             __syncwarp();
-            if (distinct > kWarpCap) { overflow = true; break; }
+            if (distinct > CAP) { overflow = true; break; }
         }
     }
     if (lane == 0) {
@@ -90,7 +119,10 @@ k_sym_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
             big[atomicAdd(nbig, 1)] = row;
         } else {
             count[row] = distinct;
+            if (!SMALL && distinct > kSmallCap) mid[atomicAdd(nmid, 1)] = row;
         }
+    }
+    __syncwarp();
     }
 }
 
@@ -192,53 +224,35 @@ k_sym_wide(int32_t nwide, const int32_t* __restrict__ rows, const int32_t* __res
     }
 }
 
-// exclusive scan of counts into ptr (m + 1 entries) by one block
-__global__ void __launch_bounds__(1024)
-k_scan(int32_t m, const int32_t* __restrict__ count, int32_t* __restrict__ ptr,
-       int* __restrict__ err) {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = ((int64_t)m + 1023) / 1024;
-    const int64_t b = t * chunk, e = min((int64_t)m, b + chunk);
-    long long s = 0;
-    for (int64_t i = b; i < e; ++i) s += count[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele
-        long long v = (t >= o) ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    long long run = (t == 0) ? 0 : part[t - 1];
-    if (part[1023] >= (1LL << 31) - 1) {
-        if (t == 0) atomicOr(err, 4);
-        return;
-    }
-    for (int64_t i = b; i < e; ++i) {
-        ptr[i] = (int32_t)run;
-        run += count[i];
-    }
-    if (t == 1023) ptr[m] = (int32_t)part[1023];
-}
-
 // -------------------------------------------------------------- numeric
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+template <bool SMALL>
+__global__ void __launch_bounds__((SMALL ? 8 : kWarpsPerBlock) * 32)
 k_num_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict__ ac,
            const double* __restrict__ av, const int32_t* __restrict__ bp,
            const int32_t* __restrict__ bc, const double* __restrict__ bv,
-           const int32_t* __restrict__ count, const int32_t* __restrict__ cp,
-           int32_t* __restrict__ cc, double* __restrict__ cv, int* __restrict__ err) {
+           const int32_t* __restrict__ count, const int32_t* __restrict__ mid, const int32_t* __restrict__ nmid,
+           const int32_t* __restrict__ cp, int32_t* __restrict__ cc, double* __restrict__ cv,
+           int* __restrict__ err) {
+    constexpr int WARPS = SMALL ? 8 : kWarpsPerBlock;
+    constexpr int SLOTS = SMALL ? kSmallSlots : kWarpSlots;
+    constexpr int CAP = SMALL ? kSmallCap : kWarpCap;
     extern __shared__ unsigned char raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kWarpsPerBlock + warp;
-    if (row >= m) return;
-    if (count[row] < 0 || count[row] > kWarpCap) return;  // handled by the block kernel
-    double* vals = reinterpret_cast<double*>(raw) + warp * kWarpSlots;
-    int* keys = reinterpret_cast<int*>(reinterpret_cast<double*>(raw) + kWarpsPerBlock * kWarpSlots) +
-                warp * (kWarpSlots + kWarpCap);
-    int* lst = keys + kWarpSlots;  // compacted slot list, kWarpCap entries
-    for (int i = lane; i < kWarpSlots; i += 32) { keys[i] = kEmpty; vals[i] = 0.0; }
+    // rows of at most kSmallCap columns go to the small instance (over all
+    // rows), rows of up to kWarpCap to the large one (over the list the
+    // symbolic phase made), longer ones to the block kernels
+    const int nrows = SMALL ? m : *nmid;
+    for (int w = blockIdx.x * WARPS + warp; w < nrows; w += (SMALL ? nrows : gridDim.x * WARPS)) {
+    const int row = SMALL ? w : mid[w];
+    if (count[row] < 0 || count[row] > CAP) continue;
+    double* vals = reinterpret_cast<double*>(raw) + warp * SLOTS;
+    int* keys = reinterpret_cast<int*>(reinterpret_cast<double*>(raw) + WARPS * SLOTS) + warp * (SLOTS + CAP);
+    int* lst = keys + SLOTS;  // compacted slot list, CAP entries
+    // a table of twice the row's column count (at least 32 slots)
+    int slots = 32;
+    while (slots < SLOTS && slots < 2 * count[row]) slots <<= 1;
+    const unsigned mask = (unsigned)slots - 1u;
+    for (int i = lane; i < slots; i += 32) { keys[i] = kEmpty; vals[i] = 0.0; }
     __syncwarp();
     for (int ka = ap[row]; ka < ap[row + 1]; ++ka) {
         const int k = ac[ka];
@@ -246,7 +260,7 @@ k_num_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
         const int b0 = bp[k], b1 = bp[k + 1];
         for (int kb = b0 + lane; kb < b1; kb += 32) {  // distinct columns: no two lanes share a slot
             bool added;
-            const int sl = insert(keys, kWarpSlots - 1, bc[kb], added);
+            const int sl = insert(keys, mask, bc[kb], added);
             if (sl < 0) atomicOr(err, 1);
             else vals[sl] = __dadd_rn(vals[sl], __dmul_rn(a, bv[kb]));
         }
@@ -254,19 +268,19 @@ k_num_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
     }
     // compact occupied slots (in slot order), then rank-sort by column
     int base = 0;
-    for (int i0 = 0; i0 < kWarpSlots; i0 += 32) {
+    for (int i0 = 0; i0 < slots; i0 += 32) {
         const bool occ = keys[i0 + lane] != kEmpty;
         const unsigned msk = __ballot_sync(0xffffffffu, occ);
         const int pos = base + __popc(msk & ((1u << lane) - 1u));
-        if (occ && pos < kWarpCap) lst[pos] = i0 + lane;
+        if (occ && pos < CAP) lst[pos] = i0 + lane;
         base += __popc(msk);
     }
     __syncwarp();
     const int n = base;
     const int out0 = cp[row];
-    if (n != count[row] || n > kWarpCap) {  // symbolic and numeric disagree: write nothing
+    if (n != count[row] || n > CAP) {  // symbolic and numeric disagree: write nothing
         if (lane == 0) atomicOr(err, 1);
-        return;
+        continue;
     }
     for (int e = lane; e < n; e += 32) {
         const int key = keys[lst[e]];
@@ -274,6 +288,8 @@ k_num_warp(int32_t m, const int32_t* __restrict__ ap, const int32_t* __restrict_
         for (int j = 0; j < n; ++j) rank += keys[lst[j]] < key;
         cc[out0 + rank] = key;
         cv[out0 + rank] = vals[lst[e]];
+    }
+    __syncwarp();
     }
 }
 
@@ -430,18 +446,28 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     S.out = &C;
     int32_t* count = S.get<int32_t>(m > 0 ? m : 1);
     int32_t* big = S.get<int32_t>(m > 0 ? m : 1);
-    int32_t* nbig = S.get<int32_t>(2);  // [0]: rows for the block kernels, [1]: wide rows
+    int32_t* nbig = S.get<int32_t>(4);  // [0]: rows for the block kernels, [1]: wide rows,
+                                        // [2]: rows for the large symbolic, [3]: the large numeric warp kernel
     int32_t* wide = S.get<int32_t>(m > 0 ? m : 1);
+    int32_t* lst = S.get<int32_t>(m > 0 ? m : 1);
+    int32_t* mid = S.get<int32_t>(m > 0 ? m : 1);
     int* err = S.get<int>(1);
-    AMG_CUDA(cudaMemsetAsync(nbig, 0, 2 * sizeof(int32_t), s));
+    AMG_CUDA(cudaMemsetAsync(nbig, 0, 4 * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     C.ptr = dev_alloc_async<int32_t>(m + 1 + kPad, s);
     AMG_CUDA(cudaMemsetAsync(C.ptr, 0, (m + 1 + kPad) * sizeof(int32_t), s));
 
-    const unsigned wgrid = (unsigned)((m + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const unsigned sgrid = (unsigned)((m + 7) / 8);
     if (m > 0) {
-        k_sym_warp<<<wgrid, kWarpsPerBlock * 32, 0, s>>>(m, A.ptr, A.col, B.ptr, B.col, count, big,
-                                                          nbig, err);
+        k_sym_warp<true><<<sgrid, 8 * 32, 0, s>>>(m, A.ptr, A.col, B.ptr, B.col, count, big, nbig, lst,
+                                                   nbig + 2, mid, nbig + 3, err);
+        AMG_CUDA(cudaGetLastError());
+        int32_t hl = 0;  // rows for the large instance: a warp each
+        AMG_CUDA(cudaMemcpyAsync(&hl, nbig + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (hl > 0)
+            k_sym_warp<false><<<(unsigned)((hl + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
+                m, A.ptr, A.col, B.ptr, B.col, count, big, nbig, lst, nbig + 2, mid, nbig + 3, err);
         AMG_CUDA(cudaGetLastError());
     }
     int32_t hbig = 0;
@@ -451,6 +477,7 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
     const size_t num_block_smem = kBlockSlots * (sizeof(double) + sizeof(int)) + kBlockCap * sizeof(int);
     const size_t num_warp_smem = kWarpsPerBlock * (kWarpSlots * (sizeof(double) + sizeof(int)) +
                                                    kWarpCap * sizeof(int));
+    const size_t num_small_smem = 8 * (kSmallSlots * (sizeof(double) + sizeof(int)) + kSmallCap * sizeof(int));
     if (hbig > 0) {
         AMG_CUDA(cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sym_smem));
@@ -479,27 +506,28 @@ void device_spgemm(const DevCsr& A, const DevCsr& B, DevCsr& C, cudaStream_t s) 
                                                         count);
         AMG_CUDA(cudaGetLastError());
     }
-    k_scan<<<1, 1024, 0, s>>>(m, count, C.ptr, err);
-    AMG_CUDA(cudaGetLastError());
-    int32_t nnz = 0;
     int herr = 0;
-    AMG_CUDA(cudaMemcpyAsync(&nnz, C.ptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA(cudaStreamSynchronize(s));
-    if (herr) {
-        if (herr & 4) fail(AMG_ERR_TOO_LARGE, "Galerkin product has more than 2^31 nonzeros");
-        fail(AMG_ERR_CUDA, "sparse product symbolic phase: hash table overflow");
-    }
+    if (herr) fail(AMG_ERR_CUDA, "sparse product symbolic phase: hash table overflow");
+    const int64_t nnz = dev_exclusive_scan(count, C.ptr, m, s);  // TOO_LARGE above 2^31 - 1
     C.nnz = nnz;
     C.col = dev_alloc_async<int32_t>(nnz + kPad, s);
     C.val = dev_alloc_async<double>(nnz + kPad, s);
     AMG_CUDA(cudaMemsetAsync(C.col, 0, (nnz + kPad) * sizeof(int32_t), s));
     AMG_CUDA(cudaMemsetAsync(C.val, 0, (nnz + kPad) * sizeof(double), s));
     if (m > 0) {
-        AMG_CUDA(cudaFuncSetAttribute(k_num_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        AMG_CUDA(cudaFuncSetAttribute(k_num_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)num_warp_smem));
-        k_num_warp<<<wgrid, kWarpsPerBlock * 32, num_warp_smem, s>>>(
-            m, A.ptr, A.col, A.val, B.ptr, B.col, B.val, count, C.ptr, C.col, C.val, err);
+        k_num_warp<true><<<sgrid, 8 * 32, num_small_smem, s>>>(
+            m, A.ptr, A.col, A.val, B.ptr, B.col, B.val, count, mid, nbig + 3, C.ptr, C.col, C.val, err);
+        int32_t hm = 0;
+        AMG_CUDA(cudaMemcpyAsync(&hm, nbig + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (hm > 0)
+            k_num_warp<false><<<(unsigned)((hm + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32,
+                                num_warp_smem, s>>>(m, A.ptr, A.col, A.val, B.ptr, B.col, B.val, count, mid, nbig + 3,
+                                                    C.ptr, C.col, C.val, err);
         AMG_CUDA(cudaGetLastError());
     }
     if (hbig > 0) {
