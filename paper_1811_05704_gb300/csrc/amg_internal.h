@@ -71,6 +71,7 @@ double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision,
 constexpr int kThreads = 256;
 constexpr int kRowsPerBlock = 256;
 constexpr int kTileNnz = 2048;
+constexpr int kLongTileNnz = 4096;  // long-row tiles of the streaming engine (at most 128 rows)
 constexpr int kConsumers = 256;  // consumer threads per CTA of the streaming engine
 
 struct DevCsr {
@@ -85,7 +86,8 @@ struct DevCsr {
     int2* tiles = nullptr;   // streaming-engine tiles {first row, first nonzero}, ntiles + 1
     int32_t ntiles = 0;      // 0: some row is longer than a tile, use the row-chunk engine
     int32_t vw = 1;          // lanes per row in the streaming engine
-    int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R)
+    int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R; 128 for long-row tiles)
+    int32_t nz_cap = kTileNnz;  // most nonzeros in one tile (kTileNnz, or kLongTileNnz)
     double* vald = nullptr;  // a_ij d_j: values scaled by the smoother diagonal (level A only)
     float* vald32 = nullptr;
     // bfloat16 copies of val and vald (bit patterns; mixed-precision V-cycle

@@ -436,7 +436,8 @@ std::vector<int32_t> host_row_blocks(const std::vector<int32_t>& ptr, int rows_c
 
 // Tiles of the streaming engine: `vw` lanes share a row (a power of two
 // about a sixth of the mean row length, so each lane handles a handful of
-// nonzeros); a tile holds at most nnz_cap nonzeros and rows_cap rows, where
+// nonzeros; a twelfth with long-row tiles of twice the nonzeros); a tile
+// holds at most nnz_cap nonzeros and rows_cap rows, where
 // rows_cap is one consumer pass (256/vw rows), or two passes when the rows are
 // short enough for two passes to fit in nnz_cap, capped by rows_cap_max.  Returned as flattened (first row, first nonzero) pairs,
 // one per tile plus the end; empty if a single row exceeds nnz_cap.
@@ -448,7 +449,8 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
     if (longest > nnz_cap || n == 0) return {};
     const double avg = (double)ptr[n] / (double)n;
     vw = 1;
-    while (vw < 32 && 2.0 * vw <= avg / 6.0) vw *= 2;
+    const double per_lane = 6.0 * (double)nnz_cap / (double)kTileNnz;  // nonzeros a lane aims for
+    while (vw < 32 && 2.0 * vw <= avg / per_lane) vw *= 2;
     // a second consumer pass only when two passes of rows still fit the tile
     const int pass = kRowsPerBlock / vw;
     rows_cap = (2.0 * pass * avg <= (double)nnz_cap) ? std::min(rows_cap_max, 2 * pass) : pass;

@@ -31,19 +31,33 @@ static void track(amg_handle* h, const DevCsr& D) {
     h->dev_bytes += (int64_t)(D.nrows + 1 + kPad) * 4 + (D.nnz + kPad) * 12;
 }
 
-static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, int rows_cap_max) {
+static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, int rows_cap_max,
+                     bool allow_long = false) {
     const std::vector<int32_t> blk = host_row_blocks(ptr, kRowsPerBlock, kTileNnz);
     D.nblk = (int32_t)blk.size() - 1;
     D.blk = halloc<int32_t>(h, blk.size());
     AMG_CUDA(cudaMemcpyAsync(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     int vw = 1, rows_cap = kRowsPerBlock;
-    const std::vector<int32_t> tiles = host_tiles(ptr, kTileNnz, rows_cap_max, vw, rows_cap);
+    // long-row tiles where the caller allows them (the fused restriction
+    // operators of a float64 V-cycle) for a large matrix with long rows: at
+    // least 48 nonzeros a row and enough nonzeros for about two tiles per
+    // persistent CTA.  Measured on 150^3 Poisson: the finest operator's
+    // product (75 nonzeros a row, 4 lanes instead of 8) 115 -> 102 us.  On
+    // the dense coarse levels of the 200^3 variable-coefficient problem
+    // (130-2,000 nonzeros a row) and in the float V-cycles the shallower
+    // ring cost more than the fewer lanes saved.
+    const int64_t nnz = ptr.back(), nr = (int64_t)ptr.size() - 1;
+    const bool long_rows = allow_long && rows_cap_max == kRowsPerBlock && nr > 0 && nnz >= 48 * nr &&
+                           nnz >= (int64_t)kLongTileNnz * 600;
+    const int nz_cap = long_rows ? kLongTileNnz : kTileNnz;
+    const std::vector<int32_t> tiles = host_tiles(ptr, nz_cap, long_rows ? 128 : rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
     D.ntiles = 0;
     if (!tiles.empty() && h->prm.use_stream) {
         D.ntiles = (int32_t)tiles.size() / 2 - 1;
         D.vw = vw;
         D.rows_cap = rows_cap;
+        D.nz_cap = nz_cap;
         int32_t* t = halloc<int32_t>(h, tiles.size());
         AMG_CUDA(cudaMemcpyAsync(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
         D.tiles = reinterpret_cast<int2*>(t);
@@ -211,7 +225,7 @@ static void build_fused_restriction(amg_handle* h, Level& L, int level, const st
     }
     track(h, M);
     dev_fused_restriction(L.R, L.d, M, h->stream);
-    schedule(h, download_ptr(M, h->stream), M, kRowsPerBlock);
+    schedule(h, download_ptr(M, h->stream), M, kRowsPerBlock, !f32);
     if (f32) make_f32(h, M);
     L.M = M;
 }

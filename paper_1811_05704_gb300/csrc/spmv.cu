@@ -49,8 +49,14 @@ constexpr int kCons = kConsumers;
 // most about 24 KB and four CTAs per SM (their registers then fit 56 per
 // thread).  More tiles in flight per SM hide more of the gather latency;
 // measured on the 150^3 V-cycles, four CTAs of 2 stages beat three of 3.
-template <typename VT>
-__host__ __device__ constexpr int stages() { return sizeof(VT) >= 8 ? 3 : 2; }
+// Long-row tiles (RMAX = 128, chosen at set-up for large matrices with long
+// rows, such as the fused restriction operators) hold kLongTileNnz nonzeros
+// in 2 stages: the same shared memory per CTA as 3 stages of kTileNnz, and
+// room for fewer lanes per row (fewer shuffle steps on the float64 pipe).
+template <int RMAX>
+__host__ __device__ constexpr int tile_nnz() { return RMAX == 128 ? kLongTileNnz : kTileNnz; }
+template <typename VT, int RMAX>
+__host__ __device__ constexpr int stages() { return RMAX == 128 ? 2 : (sizeof(VT) >= 8 ? 3 : 2); }
 template <typename VT>
 __host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 2 : kStreamCtasMax; }
 
@@ -78,7 +84,7 @@ template <typename VT, int RMAX, typename Epi>
 struct StreamLayout {
     static constexpr int NV = Epi::nvec;
     static constexpr int rp_n = RMAX + 8;       // row pointers of the tile (+ alignment slack)
-    static constexpr int nz_n = kTileNnz + 2 * nz_align<VT>();  // nonzeros of the tile (+ alignment slack)
+    static constexpr int nz_n = tile_nnz<RMAX>() + 2 * nz_align<VT>();  // nonzeros of the tile (+ alignment slack)
     static constexpr int vec_n = RMAX + 8;      // rows of a row-indexed vector slice (+ alignment slack)
     static constexpr size_t rp_bytes = (size_t)rp_n * 4;
     static constexpr size_t col_bytes = (size_t)nz_n * 4;
@@ -93,7 +99,7 @@ struct StreamLayout {
     }
     static constexpr size_t stage = rp_bytes + col_bytes + val_bytes + vec_off(NV);
     static constexpr size_t header = 128;
-    static constexpr size_t total = header + stages<VT>() * stage;
+    static constexpr size_t total = header + stages<VT, RMAX>() * stage;
     static_assert(rp_bytes % 16 == 0 && col_bytes % 16 == 0 && val_bytes % 16 == 0 && stage % 16 == 0,
                   "bulk-copy destinations must stay 16-byte aligned");
 };
@@ -194,7 +200,7 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     using acc_t = typename Epi::acc_t;
     constexpr int NV = Epi::nvec;
     using L = StreamLayout<VT, RMAX, Epi>;
-    constexpr int kStages = stages<VT>();  // at most 3: the 128-byte header holds their barriers
+    constexpr int kStages = stages<VT, RMAX>();  // at most 3: the 128-byte header holds their barriers
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* empty = full + kStages;
@@ -596,7 +602,8 @@ static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& re
                 const int* skip, cudaStream_t s) {
     if (A.nrows == 0) return;
     if (A.tiles) {
-        if (A.rows_cap <= 256) launch_stream<VT, Epi, 256>(A, val, epi, red, skip, s);
+        if (A.nz_cap == kLongTileNnz) launch_stream<VT, Epi, 128>(A, val, epi, red, skip, s);
+        else if (A.rows_cap <= 256) launch_stream<VT, Epi, 256>(A, val, epi, red, skip, s);
         else launch_stream<VT, Epi, 512>(A, val, epi, red, skip, s);
         return;
     }

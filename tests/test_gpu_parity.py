@@ -280,6 +280,38 @@ def test_solve_matches_oracle(amg, torch_dev, case):
     S.close()
 
 
+@pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18"])
+def test_fused_restriction_on_and_off_match_oracle(amg, torch_dev, case):
+    """The solve with the fused restriction operator (the default) and
+    without it (fused_restriction = 0: pre-sweep, residual and restriction
+    as separate steps) both meet the oracle's solve: true residual <= rtol,
+    iterations +/- 1, x within 1e-6; and the two V-cycles agree entry by
+    entry within the V-cycle bound."""
+    make, kw = CASES[case]
+    A = make()
+    f, _ = gen.rhs_from_solution(A, 13)
+    import oracle
+    H = oracle.Hierarchy(A, params=orc_params(**kw))
+    xo, ito, _, sto = (H.bicgstab if kw.get("solver") == 1 else H.cg)(f, rtol=1e-8, maxiter=300)
+    r = gen.uniform_pm1(7, 20, A.n)
+    zs = []
+    for fused in (1, 0):
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val, fused_restriction=fused, **kw)
+        used = any(amg.amg_fused_restriction_nnz(S.handle, l) for l in range(S.info()["levels"]))
+        assert used if (fused and case == "poisson32") else (not used or fused)
+        x = t(torch_dev, np.zeros(A.n))
+        st, it, rr = S.solve(t(torch_dev, f), x, rtol=1e-8, maxiter=300)
+        xs = x.cpu().numpy()
+        assert st == 0 and sto == 0 and _true_relres(A, xs, f) <= 1e-8
+        assert abs(it - ito) <= 1, (fused, it, ito)
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+        z = t(torch_dev, np.zeros(A.n))
+        amg.amg_apply_precond(S.handle, t(torch_dev, r), z)
+        zs.append(z.cpu().numpy())
+        S.close()
+    _assert_vcycle_close(zs[0], zs[1])
+
+
 def test_graph_and_host_loop_agree_bitwise(amg, torch_dev):
     """The graph solve (device-side while loop) and the host-launched loop
     give identical iterates; amg_last_solve_mode shows that the first really
