@@ -13,7 +13,10 @@
 //                     loads it directly
 //   xg(c)             the gathered operand g for column c
 //   Pre load(i, vt)   row-indexed inputs of row i (from the tile's copies)
-//   store(i, s, pre, d0, d1)   write the outputs of row i, set dot terms
+//   store(i, s, pre, d0, d1)   write the outputs of row i and add its dot
+//                     terms to the running sums d0, d1 (a fused multiply-add
+//                     each; an epilogue with fewer than two dots leaves the
+//                     unused sums alone, so they cost no float64 add)
 // and optionally
 //   kSeed, seed(pre)  seeded accumulation for outputs of the form seed - s
 //                     (kSeed = -1: a residual f - A x) or seed + s (kSeed =
@@ -81,7 +84,7 @@ struct EpiYDot {  // y = A x, dot w.y
     __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double& d0, double&) const {
         y[r] = s;
-        d0 = p.w * s;
+        d0 = fma(p.w, s, d0);
     }
 };
 
@@ -98,8 +101,8 @@ struct EpiYDot2 {  // y = A x, dots y.y and y.w
     __device__ Pre load(int r, const VecTile& v) const { return {v.at<double>(0, r)}; }
     __device__ void store(int r, double s, const Pre& p, double& d0, double& d1) const {
         y[r] = s;
-        d0 = s * s;
-        d1 = s * p.w;
+        d0 = fma(s, s, d0);
+        d1 = fma(s, p.w, d1);
     }
 };
 
@@ -165,7 +168,7 @@ struct EpiSmooth {  // y = x + d (f - A x) ; optional w.y
     __device__ void store(int r, double res, const Pre& p, double& d0, double&) const {
         const double val = p.x + p.d * res;
         y[r] = val;
-        if (DOT) d0 = p.w * val;
+        if (DOT) d0 = fma(p.w, val, d0);
     }
 };
 
@@ -192,7 +195,7 @@ struct EpiSmoothDotF {
     __device__ void store(int r, double res, const Pre& p, double& d0, double&) const {
         const double val = p.x + p.d * res;
         y[r] = val;
-        d0 = p.f * val;
+        d0 = fma(p.f, val, d0);
     }
 };
 
@@ -219,8 +222,8 @@ struct EpiResid {
         r[i] = v;
         if (r2) r2[i] = v;
         if constexpr (F32) r32[i] = (float)v;
-        d0 = v * v;
-        d1 = p.f * p.f;
+        d0 = fma(v, v, d0);
+        d1 = fma(p.f, p.f, d1);
     }
 };
 
@@ -350,7 +353,7 @@ struct EpiSmooth32 {
         const float val = p.x + p.d * (p.f - s);
         if constexpr (F64OUT) y64[r] = (double)val;
         else y32[r] = val;
-        if constexpr (DOT) d0 = p.w * (double)val;
+        if constexpr (DOT) d0 = fma(p.w, (double)val, d0);
     }
 };
 

@@ -453,7 +453,7 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
     while (vw < 32 && 2.0 * vw <= avg / per_lane) vw *= 2;
     // a second consumer pass only when two passes of rows still fit the tile
     const int pass = kRowsPerBlock / vw;
-    rows_cap = (2.0 * pass * avg <= (double)nnz_cap) ? std::min(rows_cap_max, 2 * pass) : pass;
+    rows_cap = std::min(rows_cap_max, (2.0 * pass * avg <= (double)nnz_cap) ? 2 * pass : pass);
     const std::vector<int32_t> rows = host_row_blocks(ptr, rows_cap, nnz_cap);
     std::vector<int32_t> out;
     out.reserve(2 * rows.size());

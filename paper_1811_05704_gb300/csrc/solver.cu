@@ -54,6 +54,12 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     D.tiles = nullptr;
     D.ntiles = 0;
     if (!tiles.empty() && h->prm.use_stream) {
+        // every tile must fit the shared-memory slots of the kernel instance
+        // that run() picks for it (RMAX rows, nz_cap nonzeros)
+        const int rmax = long_rows ? 128 : (rows_cap <= kRowsPerBlock ? kRowsPerBlock : 2 * kRowsPerBlock);
+        for (size_t t = 0; t + 3 < tiles.size(); t += 2)
+            if (tiles[t + 2] - tiles[t] > rmax || tiles[t + 3] - tiles[t + 1] > nz_cap)
+                fail(AMG_ERR_TOO_LARGE, "streaming tile exceeds its kernel's row or nonzero slots");
         D.ntiles = (int32_t)tiles.size() / 2 - 1;
         D.vw = vw;
         D.rows_cap = rows_cap;

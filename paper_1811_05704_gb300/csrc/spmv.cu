@@ -43,22 +43,24 @@ namespace amg {
 // the solve overlap their pipeline fill with the predecessor's tail.
 constexpr int kCons = kConsumers;
 
-// Ring depth and resident CTAs per SM.  A float64 kernel keeps 3 stages of
-// about 34 KB and two CTAs per SM; the float32 and bfloat16 kernels, bound by
-// gather latency rather than by a pipe, trade depth for CTAs: 2 stages of at
-// most about 24 KB and four CTAs per SM (their registers then fit 56 per
-// thread).  More tiles in flight per SM hide more of the gather latency;
-// measured on the 150^3 V-cycles, four CTAs of 2 stages beat three of 3.
-// Long-row tiles (RMAX = 128, chosen at set-up for large matrices with long
-// rows, such as the fused restriction operators) hold kLongTileNnz nonzeros
-// in 2 stages: the same shared memory per CTA as 3 stages of kTileNnz, and
-// room for fewer lanes per row (fewer shuffle steps on the float64 pipe).
+// Ring depth and resident CTAs per SM.  Every kernel keeps a ring of 2
+// stages.  A float64 stage is about 34 KB, and three CTAs fit an SM; the
+// float32 and bfloat16 stages (at most about 24 KB) fit four CTAs (their
+// registers then fit 56 per thread).  More CTAs hide more of the gather
+// latency than a deeper ring: measured on the 150^3 V-cycles, four float32
+// CTAs of 2 stages beat three of 3, and three float64 CTAs of 2 stages beat
+// two of 3 (FP64 solve 8.92 -> 8.72 ms; 200^3 variable coefficients 626 ->
+// 588 ms).  Long-row tiles (RMAX = 128, chosen at set-up for large matrices
+// with long rows, such as the fused restriction operators) hold
+// kLongTileNnz nonzeros, about 50 KB a stage in float64, so two such CTAs
+// fit an SM; they leave room for fewer lanes per row (fewer shuffle steps on
+// the float64 pipe).
 template <int RMAX>
 __host__ __device__ constexpr int tile_nnz() { return RMAX == 128 ? kLongTileNnz : kTileNnz; }
 template <typename VT, int RMAX>
-__host__ __device__ constexpr int stages() { return RMAX == 128 ? 2 : (sizeof(VT) >= 8 ? 3 : 2); }
+__host__ __device__ constexpr int stages() { return 2; }
 template <typename VT>
-__host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 2 : kStreamCtasMax; }
+__host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 3 : kStreamCtasMax; }
 
 __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 
@@ -336,18 +338,8 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                             sumB += __shfl_xor_sync(0xffffffffu, sumB, o, vw);
                         }
                         if (lane == 0) {
-                            double e0 = 0.0, e1 = 0.0;
-                            if (actA) {
-                                epi.store(rowA, sumA, preA, e0, e1);
-                                d0 += e0;
-                                d1 += e1;
-                            }
-                            if (actB) {
-                                e0 = e1 = 0.0;
-                                epi.store(rowB, sumB, preB, e0, e1);
-                                d0 += e0;
-                                d1 += e1;
-                            }
+                            if (actA) epi.store(rowA, sumA, preA, d0, d1);
+                            if (actB) epi.store(rowB, sumB, preB, d0, d1);
                         }
                     }
                 } else
@@ -378,12 +370,7 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                         }
                     }
                     for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
-                    if (active && lane == 0) {
-                        double e0 = 0.0, e1 = 0.0;
-                        epi.store(row, sum, pre, e0, e1);
-                        d0 += e0;
-                        d1 += e1;
-                    }
+                    if (active && lane == 0) epi.store(row, sum, pre, d0, d1);
                 }
             }
             __syncwarp();
