@@ -84,9 +84,11 @@ typedef struct {
     int use_stream;        /* [1] sparse products stream the matrix through shared memory with
                               bulk asynchronous copies (persistent kernels); 0 = row-chunk
                               kernels with plain loads.  Results agree to rounding. */
-    int use_pdl;           /* [1] let consecutive sparse-product kernels overlap through
+    int use_pdl;           /* [0] let consecutive sparse-product kernels overlap through
                               programmatic dependent launch (process-wide setting, applied
-                              at each call that launches work) */
+                              at each call that launches work).  Off by default: measured
+                              slower in the solve's CUDA graph (150^3 FP64 8.72 against
+                              8.62 ms, 200^3 variable coefficients 464 against 447 ms). */
     int use_tail;          /* [0] run the small coarse levels (below about 4 million nonzeros,
                               finest level excluded) as one cooperative launch with grid-wide
                               barriers; applies when npre = npost = 1.  Off by default: inside

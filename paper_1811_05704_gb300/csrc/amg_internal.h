@@ -73,6 +73,7 @@ constexpr int kRowsPerBlock = 256;
 constexpr int kTileNnz = 2048;
 constexpr int kLongTileNnz = 4096;  // long-row tiles of the streaming engine (at most 128 rows)
 constexpr int kConsumers = 256;  // consumer threads per CTA of the streaming engine
+constexpr int kBlockRowNnz = 2048;  // long-row engine: rows this long or shorter never take a whole block
 
 struct DevCsr {
     int32_t nrows = 0, ncols = 0;
@@ -88,6 +89,9 @@ struct DevCsr {
     int32_t vw = 1;          // lanes per row in the streaming engine
     int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R; 128 for long-row tiles)
     int32_t nz_cap = kTileNnz;  // most nonzeros in one tile (kTileNnz, or kLongTileNnz)
+    int32_t rows_vw = 0;        // > 0 (no tiles): the long-row engine, with this many lanes a row
+    int32_t* brows = nullptr;   // long-row engine: rows of more than brow_min nonzeros, a block each
+    int32_t nbrows = 0, brow_min = 0;
     double* vald = nullptr;  // a_ij d_j: values scaled by the smoother diagonal (level A only)
     float* vald32 = nullptr;
     // bfloat16 copies of val and vald (bit patterns; mixed-precision V-cycle

@@ -188,7 +188,7 @@ amg_status amg_params_default(amg_params* p) {
     p->precision = AMG_PRECISION_FP64;
     p->use_graph = 1;
     p->use_stream = 1;
-    p->use_pdl = 1;
+    p->use_pdl = 0;
     p->use_tail = 0;
     p->device_setup = 1;
     p->fused_restriction = 1;

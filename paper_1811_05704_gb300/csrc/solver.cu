@@ -53,6 +53,35 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     const std::vector<int32_t> tiles = host_tiles(ptr, nz_cap, long_rows ? 128 : rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
     D.ntiles = 0;
+    D.rows_vw = 0;
+    if (tiles.empty() && h->prm.use_stream && nr > 0) {
+        // a row longer than a tile: the long-row engine.  Rows of more than
+        // brow_min nonzeros (kBlockRowNnz, or four times the mean row if that
+        // is more) take a block each; the others a group of lanes sized for
+        // about one batch of kRowBatch (8) nonzeros a lane.  Measured on the
+        // 200^3 variable-coefficient levels: with a block for every row over
+        // kBlockRowNnz, levels of 1,100-2,000 nonzeros a row ran 25% slower
+        // than with none; levels of 700-860 a row, a few rows of 6,500-8,100,
+        // ran 45% faster
+        D.brow_min = (int32_t)std::max<int64_t>(kBlockRowNnz, 4 * nnz / nr);
+        std::vector<int32_t> brows;
+        int64_t small_nnz = 0;
+        for (int64_t i = 0; i < nr; ++i) {
+            if (ptr[i + 1] - ptr[i] > D.brow_min) brows.push_back((int32_t)i);
+            else small_nnz += ptr[i + 1] - ptr[i];
+        }
+        const double avg = (double)small_nnz / (double)std::max<int64_t>(1, nr - (int64_t)brows.size());
+        int lanes = 1;
+        while (lanes < 32 && 8.0 * lanes < avg) lanes *= 2;
+        D.rows_vw = lanes;
+        D.nbrows = (int32_t)brows.size();
+        D.brows = nullptr;
+        if (!brows.empty()) {
+            D.brows = halloc<int32_t>(h, brows.size());
+            AMG_CUDA(cudaMemcpyAsync(D.brows, brows.data(), brows.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                     h->stream));
+        }
+    }
     if (!tiles.empty() && h->prm.use_stream) {
         // every tile must fit the shared-memory slots of the kernel instance
         // that run() picks for it (RMAX rows, nz_cap nonzeros)

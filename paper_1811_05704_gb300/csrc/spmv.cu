@@ -483,6 +483,117 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
     if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
 }
 
+// ------------------------------------------------------- long-row engine
+// Matrices with a row longer than a streaming tile (the dense coarse levels
+// that aggregation leaves on problems with strongly varying coefficients:
+// hundreds to thousands of nonzeros a row).  A group of vw lanes (a warp, or
+// half of one) takes a row; its lanes stride through the row's nonzeros with
+// coalesced, evict-first column and value loads, keep kRowBatch gathers in
+// flight each, accumulate with fused multiply-adds (one float64 operation a
+// nonzero, against a product and an add in the row-chunk engine) and reduce
+// with shuffles; the group's first lane runs the epilogue.  Groups take rows
+// round-robin, so a long row holds up only its own group (no tile barrier
+// couples it to other rows).  Rows of more than brow_min nonzeros (a few
+// nearly dense rows on the smallest levels; brow_min is set per matrix at
+// set-up) would leave one group far behind the rest; the whole block takes
+// those first, from a list made at set-up.
+constexpr int kRowBatch = 8;
+
+// sum -/+ the products of nonzeros k, k + step, ... < ke, kRowBatch at a time
+template <int SIGN, typename acc_t, typename VT, typename Epi>
+__device__ __forceinline__ acc_t row_partial(acc_t sum, int k, int ke, int step, const int32_t* __restrict__ col,
+                                             const VT* __restrict__ val, const Epi& epi) {
+    for (; k + (kRowBatch - 1) * step < ke; k += kRowBatch * step) {
+        int c[kRowBatch];
+        acc_t a[kRowBatch], x[kRowBatch];
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+            c[u] = ld_stream(col + k + u * step);
+            a[u] = (acc_t)ld_stream(val + k + u * step);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) x[u] = epi.xg(c[u]);
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+            if constexpr (SIGN < 0) sum -= a[u] * x[u];
+            else sum += a[u] * x[u];
+        }
+    }
+    for (; k < ke; k += step) {
+        const acc_t a = (acc_t)ld_stream(val + k);
+        if constexpr (SIGN < 0) sum -= a * epi.xg(ld_stream(col + k));
+        else sum += a * epi.xg(ld_stream(col + k));
+    }
+    return sum;
+}
+
+template <typename VT, typename Epi>
+__global__ void __launch_bounds__(kThreads)
+k_rows(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const VT* __restrict__ val,
+       int32_t nrows, int vw, const int32_t* __restrict__ brows, int32_t nbrows, int32_t brow_min, Epi epi,
+       Reduce red,
+       const int* __restrict__ skip) {
+    using acc_t = typename Epi::acc_t;
+    constexpr int SIGN = Seeding<Epi>::sign;
+    __shared__ acc_t part[kThreads / 32];
+    if (skip && *(volatile const int*)skip) return;
+    VecTile vt;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        vt.base[k] = (k < Epi::nvec) ? static_cast<const unsigned char*>(epi.vptr(k)) : nullptr;
+    vt.row0 = 0;
+    double d0 = 0.0, d1 = 0.0;
+    // the longest rows, a block each
+    for (int i = blockIdx.x; i < nbrows; i += gridDim.x) {
+        const int row = __ldg(brows + i);
+        typename Epi::Pre pre{};
+        acc_t sum = acc_t(0);
+        if (threadIdx.x == 0) {
+            pre = epi.load(row, vt);
+            if constexpr (SIGN != 0) sum = epi.seed(pre);
+        }
+        sum = row_partial<SIGN>(sum, __ldg(ptr + row) + (int)threadIdx.x, __ldg(ptr + row + 1), kThreads, col,
+                                val, epi);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            acc_t t = part[0];
+            for (int w = 1; w < kThreads / 32; ++w) t += part[w];
+            epi.store(row, t, pre, d0, d1);
+        }
+        __syncthreads();
+    }
+    // the other rows, a group of vw lanes each; every lane of a warp runs the
+    // same number of iterations (the shuffles need the whole warp): rows past
+    // the end, and rows of the list above, are inactive
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & (vw - 1);
+    const int group = tid / vw, ngroups = (gridDim.x * blockDim.x) / vw;
+    const int rounds = (nrows + ngroups - 1) / ngroups;
+    for (int it = 0; it < rounds; ++it) {
+        const int row = group + it * ngroups;
+        int kb = 0, ke = 0;
+        bool active = false;
+        if (row < nrows) {
+            kb = __ldg(ptr + row);
+            ke = __ldg(ptr + row + 1);
+            active = ke - kb <= brow_min;
+            if (!active) kb = ke = 0;
+        }
+        typename Epi::Pre pre{};
+        acc_t sum = acc_t(0);
+        if (active && lane == 0) {
+            pre = epi.load(row, vt);
+            if constexpr (SIGN != 0) sum = epi.seed(pre);
+        }
+        sum = row_partial<SIGN>(sum, kb + lane, ke, vw, col, val, epi);
+        for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
+        if (active && lane == 0) epi.store(row, sum, pre, d0, d1);
+    }
+    if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
+}
+
 static std::atomic<int> g_sm_count{0};
 // set by the thread that issues the launches (several host threads may each
 // drive a solve on their own stream)
@@ -585,6 +696,26 @@ static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const 
 }
 
 template <typename VT, typename Epi>
+static void launch_rows(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
+                        const int* skip, cudaStream_t s) {
+    static const int per_sm = [] {
+        int b = 0;
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<VT, Epi>, kThreads, 0));
+        return std::max(1, b);
+    }();
+    const int vw = A.rows_vw, per_block = kThreads / vw;
+    int grid = stream_grid((int)std::min<int64_t>(((int64_t)A.nrows + per_block - 1) / per_block, 1 << 30), per_sm);
+    if (Epi::ndot > 0) grid = std::min(grid, red.stride);
+    // launched in plain stream order, without programmatic dependent launch:
+    // with it (the kernel triggering its dependents at the start, like the
+    // streaming engine) the 200^3 variable-coefficient FP64 solve took 748
+    // instead of 506 ms
+    k_rows<VT, Epi><<<grid, kThreads, 0, s>>>(A.ptr, A.col, val, (int32_t)A.nrows, vw, A.brows, A.nbrows,
+                                              A.brow_min, epi, red, skip);
+    AMG_CUDA(cudaGetLastError());
+}
+
+template <typename VT, typename Epi>
 static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
                 const int* skip, cudaStream_t s) {
     if (A.nrows == 0) return;
@@ -592,6 +723,13 @@ static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& re
         if (A.nz_cap == kLongTileNnz) launch_stream<VT, Epi, 128>(A, val, epi, red, skip, s);
         else if (A.rows_cap <= 256) launch_stream<VT, Epi, 256>(A, val, epi, red, skip, s);
         else launch_stream<VT, Epi, 512>(A, val, epi, red, skip, s);
+        return;
+    }
+    // the long-row engine for float64 values only: the float kernels are
+    // not bound by a pipe, and there the row-chunk engine measured faster
+    // (200^3 variable coefficients, FP32 V-cycle 273 against 303 ms)
+    if (A.rows_vw && sizeof(VT) >= 8) {
+        launch_rows(A, val, epi, red, skip, s);
         return;
     }
     if (Epi::ndot > 0 && A.nblk > red.stride) fail(AMG_ERR_TOO_LARGE, "reduction buffer smaller than the grid");

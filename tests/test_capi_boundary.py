@@ -73,7 +73,7 @@ def test_params_default(lib):
     assert (p.strength_eps, p.strength_halving, p.smoother, p.jacobi_omega) == (0.08, 1, 0, 0.72)
     assert (p.npre, p.npost, p.coarse_enough, p.max_levels) == (1, 1, 500, 25)
     assert (p.max_coarse_dense, p.solver, p.precision, p.use_graph) == (4096, 0, 0, 1)
-    assert (p.use_stream, p.use_pdl, p.use_tail, p.device_setup, p.fused_restriction) == (1, 1, 0, 1, 1)
+    assert (p.use_stream, p.use_pdl, p.use_tail, p.device_setup, p.fused_restriction) == (1, 0, 0, 1, 1)
     assert lib._lib.amg_params_default(None) == lib.AMG_ERR_INVALID_ARG
 
 

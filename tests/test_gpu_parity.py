@@ -198,7 +198,7 @@ def _row_bound(ptr, col, val, x):
     return np.bincount(rows, weights=np.abs(val * x[col]), minlength=len(ptr) - 1)
 
 
-@pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18"])
+@pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18", "star40"])
 def test_level_spmv(amg, torch_dev, case):
     import oracle
     make, kw = CASES[case]
@@ -333,6 +333,26 @@ def test_graph_and_host_loop_agree_bitwise(amg, torch_dev):
         xs.append((x.cpu().numpy(), it, rr))
         S.close()
     assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
+
+
+def test_programmatic_dependent_launch_same_result(amg, torch_dev):
+    """use_pdl = 1 (consecutive streaming kernels overlap their start with
+    the predecessor's tail; off by default) changes only the scheduling:
+    the solve gives the same iterates bit for bit as with it off, in the
+    graph and from the host, on a hierarchy that uses the fused restriction
+    operators and the long-row engine (a dense row)."""
+    for A, kw in ((gen.varcoef3d(18, seed=9), {"coarse_enough": 80}), (gen.poisson3d_star(24), {})):
+        f, _ = gen.rhs_from_solution(A, 2)
+        out = []
+        for pdl, graph in ((0, 1), (1, 1), (1, 0)):
+            S = amg.Solver(A.n, A.row_ptr, A.col, A.val, use_pdl=pdl, use_graph=graph, **kw)
+            x = t(torch_dev, np.zeros(A.n))
+            st, it, rr = S.solve(t(torch_dev, f), x)
+            assert st == 0
+            out.append((it, x.cpu().numpy()))
+            S.close()
+        for it, xs in out[1:]:
+            assert it == out[0][0] and np.array_equal(xs, out[0][1])
 
 
 def test_unaligned_solution_vector(amg, torch_dev):
