@@ -50,12 +50,28 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     const bool long_rows = allow_long && rows_cap_max == kRowsPerBlock && nr > 0 && nnz >= 48 * nr &&
                            nnz >= (int64_t)kLongTileNnz * 600;
     const int nz_cap = long_rows ? kLongTileNnz : kTileNnz;
-    const std::vector<int32_t> tiles = host_tiles(ptr, nz_cap, long_rows ? 128 : rows_cap_max, vw, rows_cap);
+    // Float64 values on a matrix of long, irregular rows (at least 32
+    // nonzeros a row on average and a row of at least three times the mean:
+    // the coarse levels and fused operators of problems with strongly varying
+    // coefficients) take the long-row engine instead of tiles, whose
+    // consumers wait for a tile's longest row.  Measured on 200^3 variable
+    // coefficients: level 2 (43 a row, longest 282) 308 -> 248 us, level 3
+    // (133, longest 1,167) 504 -> 382 us, the FP64 solve 449 -> 415 ms.  On
+    // 150^3 Poisson, whose levels hold rows within twice their mean, tiles
+    // stay faster (the solve 8.62 against 8.84 ms with the engine from 40
+    // nonzeros a row).
+    int64_t longest = 0;
+    for (int64_t i = 0; i < nr; ++i) longest = std::max<int64_t>(longest, ptr[i + 1] - ptr[i]);
+    const bool irregular = h->prm.precision == AMG_PRECISION_FP64 && nr > 0 && nnz >= 32 * nr &&
+                           longest * nr >= 3 * nnz;
+    const std::vector<int32_t> tiles =
+        irregular ? std::vector<int32_t>() : host_tiles(ptr, nz_cap, long_rows ? 128 : rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
     D.ntiles = 0;
     D.rows_vw = 0;
     if (tiles.empty() && h->prm.use_stream && nr > 0) {
-        // a row longer than a tile: the long-row engine.  Rows of more than
+        // a row longer than a tile, or irregular rows: the long-row engine
+        // (float64 values; float values take the row-chunk engine).  Rows of more than
         // brow_min nonzeros (kBlockRowNnz, or four times the mean row if that
         // is more) take a block each; the others a group of lanes sized for
         // about one batch of kRowBatch (8) nonzeros a lane.  Measured on the
