@@ -51,7 +51,9 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
                            nnz >= (int64_t)kLongTileNnz * 600;
     const int nz_cap = long_rows ? kLongTileNnz : kTileNnz;
     // Float64 values on a matrix of long, irregular rows (at least 32
-    // nonzeros a row on average and a row of at least three times the mean:
+    // nonzeros a row on average, a row of at least three times the mean, and
+    // at least 2^20 nonzeros; the smallest levels' products, a few tiles,
+    // measured faster in the streaming engine:
     // the coarse levels and fused operators of problems with strongly varying
     // coefficients) take the long-row engine instead of tiles, whose
     // consumers wait for a tile's longest row.  Measured on 200^3 variable
@@ -63,7 +65,7 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     int64_t longest = 0;
     for (int64_t i = 0; i < nr; ++i) longest = std::max<int64_t>(longest, ptr[i + 1] - ptr[i]);
     const bool irregular = h->prm.precision == AMG_PRECISION_FP64 && nr > 0 && nnz >= 32 * nr &&
-                           longest * nr >= 3 * nnz;
+                           longest * nr >= 3 * nnz && nnz >= (int64_t)1 << 20;
     const std::vector<int32_t> tiles =
         irregular ? std::vector<int32_t>() : host_tiles(ptr, nz_cap, long_rows ? 128 : rows_cap_max, vw, rows_cap);
     D.tiles = nullptr;
