@@ -210,7 +210,7 @@ def bytes_per_iteration(info, coarse_n):
     b += 8 * coarse_n * coarse_n + 16 * coarse_n     # dense coarsest solve
     n0, z0 = info["rows"][0], info["nnz"][0]
     b += 12 * z0 + 20 * n0                           # q = A p, p.q
-    b += 48 * n0 + 24 * n0                           # x, r update; p update
+    b += 24 * n0 + 40 * n0                           # r update; x += alpha p with the p update
     return b
 
 

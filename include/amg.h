@@ -174,7 +174,8 @@ amg_status amg_hierarchy_info(const amg_handle *h, int *levels, int64_t *rows, i
  * entry.  Per V-cycle level: pre-sweep with residual, restriction,
  * prolongation with correction, post-sweep; the dense coarsest solve reads
  * its inverse.  CG adds q = A p with p.q (12 Z0 + 20 n0) and the x, r, p
- * updates (72 n0); BiCGStab two V-cycles, two products and 136 n0. */
+ * updates (64 n0: r -= alpha q with r.r; x += alpha p with p = z + beta p);
+ * BiCGStab two V-cycles, two products and 136 n0. */
 amg_status amg_hierarchy_bytes(const amg_handle *h, double *bytes_per_iteration);
 
 /* Copy level matrix `which` (0 = A_l, 1 = P_l, 2 = R_l, 3 = M_l) of level l
@@ -258,7 +259,8 @@ amg_status amg_batch_tune(amg_batch *b, const double *f, double *x, double rtol,
 amg_status amg_batch_info(const amg_batch *b, int64_t *total_rows, int64_t *row_off, int *levels);
 
 /* Algorithmic bytes of one CG iteration of each system (nsys doubles), by
- * the model of amg_hierarchy_bytes, for the batch's precision. */
+ * the model of amg_hierarchy_bytes, for the batch's precision, except that
+ * the batched CG updates x together with r (72 n0 of Krylov updates). */
 amg_status amg_batch_bytes(const amg_batch *b, double *bytes_per_iteration);
 
 /* Release the batch and its device memory.  NULL is accepted. */

@@ -62,7 +62,11 @@ struct LevelSizes {
     int64_t n, nnz, nnz_p;
     int64_t nnz_m = 0;  // nonzeros of the fused restriction operator (0: not used)
 };
-double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver);
+// cg_x_deferred: the single-system CG applies x += alpha p inside the next
+// p update (64 bytes a row of Krylov updates); the batched CG updates x with
+// r (72 bytes a row).
+double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver,
+                              bool cg_x_deferred);
 
 // ---------------------------------------------------------- device CSR
 // Row-block schedule: block b of the SpMV kernel covers rows
@@ -123,6 +127,7 @@ struct KState {
     double res;      // recurrence residual / ||f||
     double relres;   // true residual / ||f|| (after the loop)
     double rho, rho_prev, alpha, omega, beta;
+    double alpha_x;  // CG: x += alpha_x p not yet applied (0: none pending)
     double dots[4];
 };
 
@@ -211,9 +216,10 @@ void launch_prolong_pre_f32(const DevCsr& P, const float* d, const float* f, con
 
 // vector kernels
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s);
-void launch_cg_pupdate(KState* st, const double* z, double* p, int64_t n, cudaStream_t s);
-void launch_cg_update(const Reduce& r, const double* p, const double* q, double* x, double* rv,
-                      int64_t n, cudaStream_t s, float* r32 = nullptr);
+void launch_cg_pupdate(KState* st, const double* z, double* p, double* x, int64_t n, cudaStream_t s);
+void launch_cg_xfinal(KState* st, const double* p, double* x, int64_t n, cudaStream_t s);
+void launch_cg_update(const Reduce& r, const double* q, double* rv, int64_t n, cudaStream_t s,
+                      float* r32 = nullptr);
 void launch_bi_pupdate(KState* st, const double* r, const double* v, double* p, int64_t n,
                        cudaStream_t s, float* p32 = nullptr);
 void launch_bi_s(const Reduce& red, const double* r, const double* v, double* sv, int64_t n,

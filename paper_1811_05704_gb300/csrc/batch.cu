@@ -19,16 +19,27 @@ namespace amg {
 
 namespace {
 
-// Sum over the block, the same total in every thread (fixed order).
+// Sum over the block, the same total in every thread (fixed order).  The
+// values are transposed through shared memory and warp 0 adds them lane by
+// lane over the warps, then across its lanes with shuffles: nwarps + 4
+// float64 add instructions issued by one warp, against a shuffle butterfly in
+// every warp plus nwarps adds in every thread (each float64 warp instruction
+// holds the SM's float64 pipe for 16 cycles on GB300).  sh: blockDim.x + 1
+// doubles.
+constexpr int kMaxBatchThreads = 1024;
 __device__ __forceinline__ double block_allsum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
+    const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
+    __syncthreads();  // the previous call's total has been read
+    sh[tid] = v;
     __syncthreads();
-    if (lane == 0) sh[warp] = v;
+    if (tid < 32) {
+        double t = sh[lane];
+        for (int w = 32; w < nt; w += 32) t += sh[w + lane];
+        t = warp_sum(t);
+        if (lane == 0) sh[nt] = t;
+    }
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += sh[w];
-    return t;
+    return sh[nt];
 }
 
 // row i of a CSR matrix times a gathered vector, summed in column order.  The
@@ -245,7 +256,7 @@ template <typename T>
 __global__ void k_batch_cg(const BSys* __restrict__ sys, const int* __restrict__ order, int nsys,
                            const int64_t* __restrict__ row_off, unsigned int* queue, const double* f,
                            double* x, double rtol, int maxiter, BResult* res) {
-    __shared__ double sh[32];
+    __shared__ double sh[kMaxBatchThreads + 1];
     __shared__ int next;
     for (;;) {
         if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);

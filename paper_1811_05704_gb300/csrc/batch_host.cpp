@@ -280,7 +280,7 @@ void build_batch(amg_batch* b, const amg_csr* systems) {
             std::vector<LevelSizes> sz(L);
             for (int l = 0; l < L; ++l)
                 sz[l] = {S.A[l].nrows, S.A[l].nnz(), l + 1 < L ? S.P[l].nnz() : 0};
-            b->iter_bytes[k] = krylov_iteration_bytes(sz, prm.precision, AMG_SOLVER_CG);
+            b->iter_bytes[k] = krylov_iteration_bytes(sz, prm.precision, AMG_SOLVER_CG, false);
         }
         b->row_off[k + 1] = b->row_off[k] + A0.nrows;
         b->levels[k] = L;

@@ -400,7 +400,7 @@ amg_status amg_hierarchy_bytes(const amg_handle* h, double* bytes_per_iteration)
         for (size_t l = 0; l < h->lev.size(); ++l)
             sz[l] = {h->lev[l].A.nrows, h->lev[l].A.nnz, l + 1 < h->lev.size() ? h->lev[l].P.nnz : 0,
                      h->lev[l].M.nrows > 0 ? h->lev[l].M.nnz : 0};
-        *bytes_per_iteration = krylov_iteration_bytes(sz, h->prm.precision, h->prm.solver);
+        *bytes_per_iteration = krylov_iteration_bytes(sz, h->prm.precision, h->prm.solver, true);
         return AMG_OK;
     });
 }

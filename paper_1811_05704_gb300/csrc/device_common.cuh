@@ -95,8 +95,11 @@ static __device__ void finalize(const Reduce& red, double a, double b) {
             break;
         }
         case FIN_CG_ALPHA: {
+            // the p update before this product applied the pending x update
+            st->alpha_x = 0.0;
             if (!(a > 0.0) || bad(a)) { breakdown(red); break; }
             st->alpha = st->rho / a;
+            st->alpha_x = st->alpha;  // x += alpha p, applied by the next p update or after the loop
             break;
         }
         case FIN_CG_RES: {
@@ -146,17 +149,50 @@ static __device__ void finalize(const Reduce& red, double a, double b) {
     }
 }
 
+// Block sums of a (and, for ND = 2, of b) in a fixed order, valid in thread
+// 0.  The block's values are transposed through shared memory: warp w < ND
+// adds its sum's column lane by lane over the warps, then reduces its 32
+// lanes with shuffles -- nwarps + 4 float64 add instructions a sum, issued by
+// one warp.  A shuffle butterfly in every warp issues 5 a warp and nwarps
+// more; on GB300 every float64 warp instruction holds the SM's float64 pipe
+// for 16 cycles, and the dot-producing kernels end with all their blocks
+// reducing at once.  sh: ND * blockDim.x doubles of shared memory
+// (blockDim.x a multiple of 32), free again when the call returns.
+template <int ND>
+__device__ __forceinline__ void block_sums(double a, double b, double* sh, double& ta, double& tb) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    sh[tid] = a;
+    if (ND > 1) sh[nt + tid] = b;
+    __syncthreads();
+    double t = 0.0;
+    if (warp < ND) {
+        const double* c = sh + warp * nt + lane;
+        t = c[0];
+        for (int w = 32; w < nt; w += 32) t += c[w];
+        t = warp_sum(t);
+    }
+    __syncthreads();  // every column read
+    if (ND > 1 && tid == 32) sh[0] = t;
+    if (ND > 1) __syncthreads();
+    ta = t;
+    tb = ND > 1 ? sh[0] : 0.0;
+    if (ND > 1) __syncthreads();  // sh[0] read before anyone reuses sh
+}
+
 // Per-block partial sums -> partial[], and the last block to finish sums the
 // partials in index order and runs finalize().  Deterministic for a given
 // grid size.  Must be reached by every thread of every block of the grid.
-static __device__ void reduce_finalize(const Reduce& red, double a, double b) {
-    __shared__ double sh[32];
+// ND: the number of dot products (1: b is ignored and finalize gets 0).
+// sh: ND * blockDim.x doubles of shared memory.
+template <int ND>
+static __device__ void reduce_finalize_sh(const Reduce& red, double a, double b, double* sh) {
+    static_assert(ND == 1 || ND == 2, "one or two dot products");
     __shared__ int last;
-    const double ta = block_sum(a, sh);
-    const double tb = block_sum(b, sh);
+    double ta, tb;
+    block_sums<ND>(a, b, sh, ta, tb);
     if (threadIdx.x == 0) {
         red.partial[blockIdx.x] = ta;
-        red.partial[red.stride + blockIdx.x] = tb;
+        if (ND > 1) red.partial[red.stride + blockIdx.x] = tb;
         __threadfence();
         const unsigned int ticket = atomicAdd(red.counter, 1u);
         last = (ticket == gridDim.x - 1);
@@ -167,14 +203,20 @@ static __device__ void reduce_finalize(const Reduce& red, double a, double b) {
     double sa = 0.0, sb = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         sa += __ldcg(red.partial + i);
-        sb += __ldcg(red.partial + red.stride + i);
+        if (ND > 1) sb += __ldcg(red.partial + red.stride + i);
     }
-    sa = block_sum(sa, sh);
-    sb = block_sum(sb, sh);
+    block_sums<ND>(sa, sb, sh, ta, tb);
     if (threadIdx.x == 0) {
         *red.counter = 0u;
-        finalize(red, sa, sb);
+        finalize(red, ta, tb);
     }
+}
+
+// The same with a static scratch, for kernels of at most kThreads threads.
+template <int ND>
+static __device__ void reduce_finalize(const Reduce& red, double a, double b) {
+    __shared__ double sh[ND * kThreads];
+    reduce_finalize_sh<ND>(red, a, b, sh);
 }
 
 }  // namespace amg

@@ -464,7 +464,7 @@ std::vector<int32_t> host_tiles(const std::vector<int32_t>& ptr, int nnz_cap, in
     return out;
 }
 
-double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver) {
+double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision, int solver, bool cg_x_deferred) {
     if (lev.empty()) return 0.0;
     const double e = precision == AMG_PRECISION_BF16 ? 6.0 : precision == AMG_PRECISION_FP32 ? 8.0 : 12.0;
     const double v = precision == AMG_PRECISION_FP64 ? 8.0 : 4.0;
@@ -489,6 +489,8 @@ double krylov_iteration_bytes(const std::vector<LevelSizes>& lev, int precision,
     const double spmv = 12 * z0 + 4 * n0 + 16 * n0;  // q = A p with a dot product
     if (solver == AMG_SOLVER_BICGSTAB)
         return 2 * vc + 2 * spmv + 136 * n0;         // p, s, x, r updates and the extra dots
+    if (cg_x_deferred)
+        return vc + spmv + 64 * n0;                  // r update with ||r||; x += alpha p with p = z + beta p
     return vc + spmv + 72 * n0;                      // x, r update with ||r||; p = z + beta p
 }
 

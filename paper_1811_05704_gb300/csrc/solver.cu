@@ -38,16 +38,21 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
     D.blk = halloc<int32_t>(h, blk.size());
     AMG_CUDA(cudaMemcpyAsync(D.blk, blk.data(), blk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     int vw = 1, rows_cap = kRowsPerBlock;
-    // long-row tiles where the caller allows them (the fused restriction
-    // operators of a float64 V-cycle) for a large matrix with long rows: at
-    // least 48 nonzeros a row and enough nonzeros for about two tiles per
-    // persistent CTA.  Measured on 150^3 Poisson: the finest operator's
-    // product (75 nonzeros a row, 4 lanes instead of 8) 115 -> 102 us.  On
-    // the dense coarse levels of the 200^3 variable-coefficient problem
-    // (130-2,000 nonzeros a row) and in the float V-cycles the shallower
-    // ring cost more than the fewer lanes saved.
+    // long-row tiles for the fused restriction operators of a float64
+    // V-cycle (allow_long) and the level matrices of a float64 hierarchy,
+    // when the matrix is large and its rows long: at least 24 nonzeros a row
+    // and enough nonzeros for about two tiles per persistent CTA.  Long-row
+    // tiles hold twice the nonzeros, so the same rows get half the lanes
+    // each: fewer float64 shuffle adds and epilogue instructions a row.
+    // Measured on 150^3 Poisson: the finest operator's product (75 nonzeros
+    // a row, 4 lanes instead of 8) 115 -> 102 us; level 1 (32 a row, 2 lanes
+    // instead of 4) with them, the FP64 solve 8.46 -> 8.38 ms.  On the dense
+    // coarse levels of the 200^3 variable-coefficient problem (130-2,000
+    // nonzeros a row) and in the float V-cycles the shallower ring cost more
+    // than the fewer lanes saved.
     const int64_t nnz = ptr.back(), nr = (int64_t)ptr.size() - 1;
-    const bool long_rows = allow_long && rows_cap_max == kRowsPerBlock && nr > 0 && nnz >= 48 * nr &&
+    const bool long_rows = (allow_long || h->prm.precision == AMG_PRECISION_FP64) &&
+                           rows_cap_max == kRowsPerBlock && nr > 0 && nnz >= 24 * nr &&
                            nnz >= (int64_t)kLongTileNnz * 600;
     const int nz_cap = long_rows ? kLongTileNnz : kTileNnz;
     // Float64 values on a matrix of long, irregular rows (at least 32
@@ -736,7 +741,9 @@ static Reduce with(Reduce r, int fin) {
 
 // CG (Saad Alg. 9.1, preconditioned): init forms r = f - A x and the norms;
 // each pass of the body is z = M r (with r.z), p = z + beta p, q = A p (with
-// p.q), x += alpha p, r -= alpha q (with r.r and the loop test).
+// p.q), x += alpha p, r -= alpha q (with r.r and the loop test).  The x update
+// of a pass is applied by the next pass's p update, which reads that p
+// anyway, and the last one after the loop (k_cg_xfinal).
 static void cg_init(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
     const DevCsr& A = h->lev[0].A;
     I.pre(AMG_KC_OTHER); launch_residual(A, f, x, h->r, nullptr, with(b, FIN_INIT), nullptr, I.s, h->vin32); I.post();
@@ -748,9 +755,9 @@ static void cg_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
     const int* halt = flag_ptr(h, offsetof(KState, halt));
     const Reduce rz = with(b, FIN_CG_RHO);
     issue_vcycle(h, I, h->r, h->vin32, h->z, halt, &rz);
-    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_pupdate(h->st, h->z, h->p, h->n, I.s); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_pupdate(h->st, h->z, h->p, x, h->n, I.s); I.post();
     I.pre(AMG_KC_SPMV_DOT); launch_spmv_dot(A, h->p, nullptr, h->q, with(b, FIN_CG_ALPHA), halt, I.s); I.post();
-    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_update(with(b, FIN_CG_RES), h->p, h->q, x, h->r, h->n, I.s, h->vin32); I.post();
+    I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_update(with(b, FIN_CG_RES), h->q, h->r, h->n, I.s, h->vin32); I.post();
 }
 
 // BiCGStab (van der Vorst; right-preconditioned, Saad Alg. 7.7).
@@ -787,6 +794,9 @@ static void issue_body(amg_handle* h, Issue& I, double* x, const Reduce& b) {
 }
 
 static void issue_post(amg_handle* h, Issue& I, const double* f, double* x, const Reduce& b) {
+    if (h->prm.solver != AMG_SOLVER_BICGSTAB) {
+        I.pre(AMG_KC_KRYLOV_UPDATE); launch_cg_xfinal(h->st, h->p, x, h->n, I.s); I.post();
+    }
     I.pre(AMG_KC_OTHER);
     launch_residual(h->lev[0].A, f, x, h->r, nullptr, with(b, FIN_TRUE), nullptr, I.s);
     I.post();

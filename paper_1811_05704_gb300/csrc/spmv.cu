@@ -378,7 +378,10 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
         }
     }
     if constexpr (Epi::ndot > 0) {
-        if (!stop) reduce_finalize(red, d0, d1);  // a skipped kernel contributes no dot products
+        if (!stop) {  // a skipped kernel contributes no dot products
+            __syncthreads();  // every tile consumed: the ring is free for the block sums
+            reduce_finalize_sh<Epi::ndot>(red, d0, d1, reinterpret_cast<double*>(sm + L::header));
+        }
     }
 }
 
@@ -480,7 +483,7 @@ k_spmv(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
         if constexpr (Seeding<Epi>::sign > 0) acc = epi.seed(pre) + acc;
         epi.store(r0 + tid, acc, pre, d0, d1);
     }
-    if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
+    if constexpr (Epi::ndot > 0) reduce_finalize<Epi::ndot>(red, d0, d1);
 }
 
 // ------------------------------------------------------- long-row engine
@@ -591,7 +594,7 @@ k_rows(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const V
         for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
         if (active && lane == 0) epi.store(row, sum, pre, d0, d1);
     }
-    if constexpr (Epi::ndot > 0) reduce_finalize(red, d0, d1);
+    if constexpr (Epi::ndot > 0) reduce_finalize<Epi::ndot>(red, d0, d1);
 }
 
 static std::atomic<int> g_sm_count{0};
@@ -865,48 +868,95 @@ __global__ void k_fill(double* x, double v, int64_t n) {
         x[i] = v;
 }
 
-__global__ void k_cg_pupdate(const KState* __restrict__ st, const double* __restrict__ z,
-                             double* __restrict__ p, int64_t n) {
-    if (st->halt) return;
-    const double beta = st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+// Vector kernels run a grid-stride loop that takes kVecBatch elements a
+// thread at a time (i, i + stride, ...): ld(i, v) loads element i's inputs
+// for all of them before op(i, v) uses any, so that a thread keeps
+// kVecBatch times the loads in flight (one element at a time left these
+// kernels at about half the HBM bandwidth).  op runs in element order, so
+// sums accumulate in the same order as one element at a time.
+constexpr int kVecBatch = 4;
+template <int NV, typename Ld, typename Op>
+__device__ __forceinline__ void vec_batched(int64_t n, Ld ld, Op op) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += kVecBatch * stride) {
+        double v[kVecBatch][NV];
+#pragma unroll
+        for (int u = 0; u < kVecBatch; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) ld(i, v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecBatch; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) op(i, v[u]);
+        }
+    }
 }
 
-// F32: also write the updated vector rounded to float32 (the input of a
-// float32 V-cycle); a template parameter, so that the float64 solve's kernel
-// has no conversion on its float64 pipe.
+// CG's x update is deferred by one kernel: the update of iteration k,
+// x += alpha_k p_k, runs in the p update of iteration k + 1 (which reads p_k
+// anyway), or in k_cg_xfinal after the loop.  The iterates are the same,
+// operation for operation; the residual update no longer reads p and x nor
+// writes x, 8 bytes a row less per iteration.
+//   p update:  x += alpha_x p (if pending); p = z + beta p
+__global__ void __launch_bounds__(kThreads)
+k_cg_pupdate(const KState* __restrict__ st, const double* __restrict__ z, double* __restrict__ p,
+             double* __restrict__ x, int64_t n) {
+    if (st->halt) return;
+    const double beta = st->beta, ax = st->alpha_x;
+    if (ax != 0.0) {
+        vec_batched<3>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = z[i]; v[2] = x[i]; },
+                       [&](int64_t i, const double* v) {
+                           x[i] = v[2] + ax * v[0];
+                           p[i] = v[1] + beta * v[0];
+                       });
+    } else {
+        vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = z[i]; },
+                       [&](int64_t i, const double* v) { p[i] = v[1] + beta * v[0]; });
+    }
+}
+
+// The pending x update after the loop (whatever ended it).
+__global__ void __launch_bounds__(kThreads)
+k_cg_xfinal(const KState* __restrict__ st, const double* __restrict__ p, double* __restrict__ x, int64_t n) {
+    const double ax = st->alpha_x;
+    if (ax == 0.0) return;
+    vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = x[i]; },
+                   [&](int64_t i, const double* v) { x[i] = v[1] + ax * v[0]; });
+}
+
+// r -= alpha q with r.r.  F32: also write the updated vector rounded to
+// float32 (the input of a float32 V-cycle); a template parameter, so that the
+// float64 solve's kernel has no conversion on its float64 pipe.
 template <bool F32>
 __global__ void __launch_bounds__(kThreads)
-k_cg_update(Reduce red, const double* __restrict__ p, const double* __restrict__ q,
-            double* __restrict__ x, double* __restrict__ r, float* __restrict__ r32, int64_t n) {
+k_cg_update(Reduce red, const double* __restrict__ q, double* __restrict__ r, float* __restrict__ r32,
+            int64_t n) {
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += alpha * p[i];
-        const double v = r[i] - alpha * q[i];
-        r[i] = v;
-        if constexpr (F32) r32[i] = (float)v;
-        acc += v * v;
-    }
-    reduce_finalize(red, acc, 0.0);
+    vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = r[i]; v[1] = q[i]; },
+                   [&](int64_t i, const double* v) {
+                       const double t = v[0] - alpha * v[1];
+                       r[i] = t;
+                       if constexpr (F32) r32[i] = (float)t;
+                       acc += t * t;
+                   });
+    reduce_finalize<1>(red, acc, 0.0);
 }
 
 template <bool F32>  // as k_cg_update
-__global__ void k_bi_pupdate(const KState* __restrict__ st, const double* __restrict__ r,
-                             const double* __restrict__ v, double* __restrict__ p, float* __restrict__ p32,
-                             int64_t n) {
+__global__ void __launch_bounds__(kThreads)
+k_bi_pupdate(const KState* __restrict__ st, const double* __restrict__ r, const double* __restrict__ v,
+             double* __restrict__ p, float* __restrict__ p32, int64_t n) {
     if (st->halt) return;
     const double beta = st->beta, omega = st->omega;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double pv = r[i] + beta * (p[i] - omega * v[i]);
-        p[i] = pv;
-        if constexpr (F32) p32[i] = (float)pv;
-    }
+    vec_batched<3>(n, [&](int64_t i, double* e) { e[0] = r[i]; e[1] = p[i]; e[2] = v[i]; },
+                   [&](int64_t i, const double* e) {
+                       const double pv = e[0] + beta * (e[1] - omega * e[2]);
+                       p[i] = pv;
+                       if constexpr (F32) p32[i] = (float)pv;
+                   });
 }
 
 template <bool F32>  // as k_cg_update
@@ -916,14 +966,14 @@ k_bi_s(Reduce red, const double* __restrict__ r, const double* __restrict__ v,
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double s = r[i] - alpha * v[i];
-        sv[i] = s;
-        if constexpr (F32) s32[i] = (float)s;
-        acc += s * s;
-    }
-    reduce_finalize(red, acc, 0.0);
+    vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = r[i]; e[1] = v[i]; },
+                   [&](int64_t i, const double* e) {
+                       const double s = e[0] - alpha * e[1];
+                       sv[i] = s;
+                       if constexpr (F32) s32[i] = (float)s;
+                       acc += s * s;
+                   });
+    reduce_finalize<1>(red, acc, 0.0);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -935,22 +985,24 @@ k_bi_update(Reduce red, const double* __restrict__ rh, const double* __restrict_
     if (st->halt && !st->half) return;
     const double alpha = st->alpha;
     if (st->half) {  // converged on ||s||: x += alpha p^ and stop
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x)
-            x[i] += alpha * ph[i];
+        vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = x[i]; e[1] = ph[i]; },
+                       [&](int64_t i, const double* e) { x[i] = e[0] + alpha * e[1]; });
         return;
     }
     const double omega = st->omega;
     double a = 0.0, b = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += alpha * ph[i] + omega * sh[i];
-        const double v = sv[i] - omega * t[i];
-        r[i] = v;
-        a += v * v;
-        b += rh[i] * v;
-    }
-    reduce_finalize(red, a, b);
+    vec_batched<6>(n,
+                   [&](int64_t i, double* e) {
+                       e[0] = x[i]; e[1] = ph[i]; e[2] = sh[i]; e[3] = sv[i]; e[4] = t[i]; e[5] = rh[i];
+                   },
+                   [&](int64_t i, const double* e) {
+                       x[i] = e[0] + (alpha * e[1] + omega * e[2]);
+                       const double v = e[3] - omega * e[4];
+                       r[i] = v;
+                       a += v * v;
+                       b += e[5] * v;
+                   });
+    reduce_finalize<2>(red, a, b);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -959,12 +1011,16 @@ k_dot2(Reduce red, const double* __restrict__ a, const double* __restrict__ b,
        const int* __restrict__ skip) {
     if (skip && *skip) return;
     double s0 = 0.0, s1 = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        s0 += a[i] * b[i];
-        if (c) s1 += c[i] * d[i];
-    }
-    reduce_finalize(red, s0, s1);
+    if (c)
+        vec_batched<4>(n, [&](int64_t i, double* e) { e[0] = a[i]; e[1] = b[i]; e[2] = c[i]; e[3] = d[i]; },
+                       [&](int64_t i, const double* e) {
+                           s0 += e[0] * e[1];
+                           s1 += e[2] * e[3];
+                       });
+    else
+        vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = a[i]; e[1] = b[i]; },
+                       [&](int64_t i, const double* e) { s0 += e[0] * e[1]; });
+    reduce_finalize<2>(red, s0, s1);
 }
 
 // Coarsest level: x = A_L^{-1} f, one warp per row of the dense inverse.
@@ -1026,48 +1082,68 @@ __global__ void k_validate(int32_t n, int64_t nnz, const int32_t* __restrict__ p
     }
 }
 
+// Grid of a batched vector kernel K: one wave of the blocks that fit on the
+// SMs (K's registers decide how many), or fewer when n needs fewer for
+// kVecBatch elements a thread.  With a fixed 8 blocks an SM, kernels whose
+// registers allow 4 or 5 ran in two uneven waves.
+template <auto K>
+static int vec_grid_k(int64_t n) {
+    static const int per_sm = [] {
+        int b = 0;
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kThreads, 0));
+        return std::max(1, b);
+    }();
+    const int64_t per = (int64_t)kThreads * kVecBatch;
+    const int64_t g = std::min<int64_t>((n + per - 1) / per, stream_grid(1 << 30, per_sm));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, vec_grid(n)));  // within the reduction buffer
+}
+
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     k_fill<<<vec_grid(n), kThreads, 0, s>>>(x, v, n);
     AMG_CUDA(cudaGetLastError());
 }
 
-void launch_cg_pupdate(KState* st, const double* z, double* p, int64_t n, cudaStream_t s) {
-    k_cg_pupdate<<<vec_grid(n), kThreads, 0, s>>>(st, z, p, n);
+void launch_cg_pupdate(KState* st, const double* z, double* p, double* x, int64_t n, cudaStream_t s) {
+    k_cg_pupdate<<<vec_grid_k<k_cg_pupdate>(n), kThreads, 0, s>>>(st, z, p, x, n);
     AMG_CUDA(cudaGetLastError());
 }
 
-void launch_cg_update(const Reduce& r, const double* p, const double* q, double* x, double* rv,
-                      int64_t n, cudaStream_t s, float* r32) {
-    if (r32) k_cg_update<true><<<vec_grid(n), kThreads, 0, s>>>(r, p, q, x, rv, r32, n);
-    else k_cg_update<false><<<vec_grid(n), kThreads, 0, s>>>(r, p, q, x, rv, nullptr, n);
+void launch_cg_xfinal(KState* st, const double* p, double* x, int64_t n, cudaStream_t s) {
+    k_cg_xfinal<<<vec_grid_k<k_cg_xfinal>(n), kThreads, 0, s>>>(st, p, x, n);
+    AMG_CUDA(cudaGetLastError());
+}
+
+void launch_cg_update(const Reduce& r, const double* q, double* rv, int64_t n, cudaStream_t s, float* r32) {
+    if (r32) k_cg_update<true><<<vec_grid_k<k_cg_update<true>>(n), kThreads, 0, s>>>(r, q, rv, r32, n);
+    else k_cg_update<false><<<vec_grid_k<k_cg_update<false>>(n), kThreads, 0, s>>>(r, q, rv, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_bi_pupdate(KState* st, const double* r, const double* v, double* p, int64_t n,
                        cudaStream_t s, float* p32) {
-    if (p32) k_bi_pupdate<true><<<vec_grid(n), kThreads, 0, s>>>(st, r, v, p, p32, n);
-    else k_bi_pupdate<false><<<vec_grid(n), kThreads, 0, s>>>(st, r, v, p, nullptr, n);
+    if (p32) k_bi_pupdate<true><<<vec_grid_k<k_bi_pupdate<true>>(n), kThreads, 0, s>>>(st, r, v, p, p32, n);
+    else k_bi_pupdate<false><<<vec_grid_k<k_bi_pupdate<false>>(n), kThreads, 0, s>>>(st, r, v, p, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_bi_s(const Reduce& red, const double* r, const double* v, double* sv, int64_t n,
                  cudaStream_t s, float* s32) {
-    if (s32) k_bi_s<true><<<vec_grid(n), kThreads, 0, s>>>(red, r, v, sv, s32, n);
-    else k_bi_s<false><<<vec_grid(n), kThreads, 0, s>>>(red, r, v, sv, nullptr, n);
+    if (s32) k_bi_s<true><<<vec_grid_k<k_bi_s<true>>(n), kThreads, 0, s>>>(red, r, v, sv, s32, n);
+    else k_bi_s<false><<<vec_grid_k<k_bi_s<false>>(n), kThreads, 0, s>>>(red, r, v, sv, nullptr, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_bi_update(const Reduce& red, const double* rh, const double* ph, const double* sh,
                       const double* sv, const double* t, double* x, double* rv, int64_t n,
                       cudaStream_t s) {
-    k_bi_update<<<vec_grid(n), kThreads, 0, s>>>(red, rh, ph, sh, sv, t, x, rv, n);
+    k_bi_update<<<vec_grid_k<k_bi_update>(n), kThreads, 0, s>>>(red, rh, ph, sh, sv, t, x, rv, n);
     AMG_CUDA(cudaGetLastError());
 }
 
 void launch_dot2(const Reduce& red, const double* a, const double* b, const double* c,
                  const double* d, int64_t n, const int* skip, cudaStream_t s) {
-    k_dot2<<<vec_grid(n), kThreads, 0, s>>>(red, a, b, c, d, n, skip);
+    k_dot2<<<vec_grid_k<k_dot2>(n), kThreads, 0, s>>>(red, a, b, c, d, n, skip);
     AMG_CUDA(cudaGetLastError());
 }
 

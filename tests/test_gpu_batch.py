@@ -143,7 +143,8 @@ def test_iteration_bytes_agree_with_single_system(amg):
     hierarchy (the same hierarchy as the matrix set up alone), by the model
     written out on the hierarchy's sizes; the batched kernel does not use the
     fused restriction operator, so a single-system handle gives the same
-    count exactly when none of its levels uses one."""
+    count, less the 8 bytes a row that its deferred x update saves, exactly
+    when none of its levels uses one."""
     mats, rhs = _systems(6, 5, lo=20, hi=60)
     for precision in (0, 1):
         b, st, it, rr, sst, x, off, lev = _run(amg, mats, rhs, precision=precision)
@@ -155,5 +156,7 @@ def test_iteration_bytes_agree_with_single_system(amg):
             want = _model_bytes(info, precision)
             assert abs(v - want) <= 1e-12 * want and v > 0
             if not any(amg.amg_fused_restriction_nnz(S.handle, l) for l in range(info["levels"])):
-                assert abs(amg.amg_hierarchy_bytes(S.handle) - want) <= 1e-12 * want
+                # the single-system CG moves x += alpha p into the p update: 8 bytes a row less
+                single = want - 8 * info["rows"][0]
+                assert abs(amg.amg_hierarchy_bytes(S.handle) - single) <= 1e-12 * single
             S.close()

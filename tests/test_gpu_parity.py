@@ -335,6 +335,43 @@ def test_graph_and_host_loop_agree_bitwise(amg, torch_dev):
     assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
 
 
+def _shifted_poisson(m, sigma):
+    """7-point Poisson minus sigma on the diagonal: symmetric, indefinite once
+    sigma exceeds the smallest eigenvalue, so CG breaks down."""
+    A = gen.poisson3d(m)
+    val = A.val.copy()
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    val[rows == A.col] -= sigma
+    return type(A)(A.n, A.row_ptr, A.col, val)
+
+
+# (m, sigma): the check that fails (Saad Alg. 9.1 needs r.z > 0 and p.q > 0)
+# and the iteration it fails in, found with the oracle's own recurrences
+BREAKDOWN_CASES = [(10, 0.5), (10, 1.0), (12, 2.0), (14, 3.0)]  # r.z at 3, p.q at 1, p.q at 0, r.z at 0
+
+
+@pytest.mark.parametrize("m,sigma", BREAKDOWN_CASES)
+def test_cg_breakdown_matches_oracle(amg, torch_dev, m, sigma):
+    """CG on an indefinite matrix stops with BREAKDOWN where the oracle does,
+    with x as of the last completed update (the x update that is still
+    pending when the loop stops is applied after it, or dropped when the
+    breakdown is in p.q), in the graph and in the host loop."""
+    import oracle
+    A = _shifted_poisson(m, sigma)
+    f, _ = gen.rhs_from_solution(A, 4)
+    xo, ito, rro, sto = oracle.Hierarchy(A, coarse_enough=50).cg(f)
+    assert sto == oracle.BREAKDOWN
+    for use_graph in (1, 0):
+        S = amg.Solver(A.n, A.row_ptr, A.col, A.val, coarse_enough=50, use_graph=use_graph)
+        x = t(torch_dev, np.zeros(A.n))
+        st, it, rr = S.solve(t(torch_dev, f), x)
+        S.close()
+        assert (st, it) == (amg.AMG_ERR_BREAKDOWN, ito), (st, it, ito)
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - xo) <= 1e-9 * max(np.linalg.norm(xo), 1e-300) or (ito == 0 and not xg.any())
+        assert abs(rr - rro) <= 1e-9 * rro
+
+
 def test_programmatic_dependent_launch_same_result(amg, torch_dev):
     """use_pdl = 1 (consecutive streaming kernels overlap their start with
     the predecessor's tail; off by default) changes only the scheduling:
