@@ -193,13 +193,16 @@ static __device__ void reduce_finalize_sh(const Reduce& red, double a, double b,
     if (threadIdx.x == 0) {
         red.partial[blockIdx.x] = ta;
         if (ND > 1) red.partial[red.stride + blockIdx.x] = tb;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(red.counter, 1u);
+        // release: this block's partials are visible before its ticket;
+        // acquire: the last block sees every block's partials (the barrier
+        // below passes that on to its other threads).  Measured against a
+        // full fence and a relaxed atomic: 150^3 FP64 solve 8.384 -> 8.361 ms.
+        unsigned int ticket;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(red.counter) : "memory");
         last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
     double sa = 0.0, sb = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         sa += __ldcg(red.partial + i);
