@@ -870,20 +870,11 @@ __global__ void k_fill(double* x, double v, int64_t n) {
 
 // Vector kernels run a grid-stride loop that takes kVecBatch elements a
 // thread at a time (i, i + stride, ...): ld(i, v) loads element i's inputs
-// for all of them before op(i, v, u) uses any (u: the element's place in
-// the batch), so that a thread keeps kVecBatch times the loads in flight.
-// A dot product keeps kVecAccs running sums a thread, element u of a batch
-// adding to sum u % kVecAccs: on GB300 a float64 operation waits long for
-// the narrow float64 pipe (short-scoreboard stalls dominated the residual
-// update with one sum), and independent sums keep more of them in flight.
+// for all of them before op(i, v) uses any, so that a thread keeps
+// kVecBatch times the loads in flight (one element at a time left these
+// kernels at about half the HBM bandwidth).  op runs in element order, so
+// sums accumulate in the same order as one element at a time.
 constexpr int kVecBatch = 4;
-constexpr int kVecAccs = 4;
-__device__ __forceinline__ double acc_total(const double* acc) {
-    double t = acc[0];
-#pragma unroll
-    for (int k = 1; k < kVecAccs; ++k) t += acc[k];
-    return t;
-}
 template <int NV, typename Ld, typename Op>
 __device__ __forceinline__ void vec_batched(int64_t n, Ld ld, Op op) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -897,7 +888,7 @@ __device__ __forceinline__ void vec_batched(int64_t n, Ld ld, Op op) {
 #pragma unroll
         for (int u = 0; u < kVecBatch; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < n) op(i, v[u], u);
+            if (i < n) op(i, v[u]);
         }
     }
 }
@@ -915,13 +906,13 @@ k_cg_pupdate(const KState* __restrict__ st, const double* __restrict__ z, double
     const double beta = st->beta, ax = st->alpha_x;
     if (ax != 0.0) {
         vec_batched<3>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = z[i]; v[2] = x[i]; },
-                       [&](int64_t i, const double* v, int) {
+                       [&](int64_t i, const double* v) {
                            x[i] = v[2] + ax * v[0];
                            p[i] = v[1] + beta * v[0];
                        });
     } else {
         vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = z[i]; },
-                       [&](int64_t i, const double* v, int) { p[i] = v[1] + beta * v[0]; });
+                       [&](int64_t i, const double* v) { p[i] = v[1] + beta * v[0]; });
     }
 }
 
@@ -931,7 +922,7 @@ k_cg_xfinal(const KState* __restrict__ st, const double* __restrict__ p, double*
     const double ax = st->alpha_x;
     if (ax == 0.0) return;
     vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = p[i]; v[1] = x[i]; },
-                   [&](int64_t i, const double* v, int) { x[i] = v[1] + ax * v[0]; });
+                   [&](int64_t i, const double* v) { x[i] = v[1] + ax * v[0]; });
 }
 
 // r -= alpha q with r.r.  F32: also write the updated vector rounded to
@@ -943,15 +934,15 @@ k_cg_update(Reduce red, const double* __restrict__ q, double* __restrict__ r, fl
             int64_t n) {
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
-    double acc[kVecAccs] = {};
+    double acc = 0.0;
     vec_batched<2>(n, [&](int64_t i, double* v) { v[0] = r[i]; v[1] = q[i]; },
-                   [&](int64_t i, const double* v, int u) {
+                   [&](int64_t i, const double* v) {
                        const double t = v[0] - alpha * v[1];
                        r[i] = t;
                        if constexpr (F32) r32[i] = (float)t;
-                       acc[u % kVecAccs] += t * t;
+                       acc += t * t;
                    });
-    reduce_finalize<1>(red, acc_total(acc), 0.0);
+    reduce_finalize<1>(red, acc, 0.0);
 }
 
 template <bool F32>  // as k_cg_update
@@ -961,7 +952,7 @@ k_bi_pupdate(const KState* __restrict__ st, const double* __restrict__ r, const 
     if (st->halt) return;
     const double beta = st->beta, omega = st->omega;
     vec_batched<3>(n, [&](int64_t i, double* e) { e[0] = r[i]; e[1] = p[i]; e[2] = v[i]; },
-                   [&](int64_t i, const double* e, int) {
+                   [&](int64_t i, const double* e) {
                        const double pv = e[0] + beta * (e[1] - omega * e[2]);
                        p[i] = pv;
                        if constexpr (F32) p32[i] = (float)pv;
@@ -974,15 +965,15 @@ k_bi_s(Reduce red, const double* __restrict__ r, const double* __restrict__ v,
        double* __restrict__ sv, float* __restrict__ s32, int64_t n) {
     if (red.st->halt) return;
     const double alpha = red.st->alpha;
-    double acc[kVecAccs] = {};
+    double acc = 0.0;
     vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = r[i]; e[1] = v[i]; },
-                   [&](int64_t i, const double* e, int u) {
+                   [&](int64_t i, const double* e) {
                        const double s = e[0] - alpha * e[1];
                        sv[i] = s;
                        if constexpr (F32) s32[i] = (float)s;
-                       acc[u % kVecAccs] += s * s;
+                       acc += s * s;
                    });
-    reduce_finalize<1>(red, acc_total(acc), 0.0);
+    reduce_finalize<1>(red, acc, 0.0);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -995,23 +986,23 @@ k_bi_update(Reduce red, const double* __restrict__ rh, const double* __restrict_
     const double alpha = st->alpha;
     if (st->half) {  // converged on ||s||: x += alpha p^ and stop
         vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = x[i]; e[1] = ph[i]; },
-                       [&](int64_t i, const double* e, int) { x[i] = e[0] + alpha * e[1]; });
+                       [&](int64_t i, const double* e) { x[i] = e[0] + alpha * e[1]; });
         return;
     }
     const double omega = st->omega;
-    double a[kVecAccs] = {}, b[kVecAccs] = {};
+    double a = 0.0, b = 0.0;
     vec_batched<6>(n,
                    [&](int64_t i, double* e) {
                        e[0] = x[i]; e[1] = ph[i]; e[2] = sh[i]; e[3] = sv[i]; e[4] = t[i]; e[5] = rh[i];
                    },
-                   [&](int64_t i, const double* e, int u) {
+                   [&](int64_t i, const double* e) {
                        x[i] = e[0] + (alpha * e[1] + omega * e[2]);
                        const double v = e[3] - omega * e[4];
                        r[i] = v;
-                       a[u % kVecAccs] += v * v;
-                       b[u % kVecAccs] += e[5] * v;
+                       a += v * v;
+                       b += e[5] * v;
                    });
-    reduce_finalize<2>(red, acc_total(a), acc_total(b));
+    reduce_finalize<2>(red, a, b);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -1019,17 +1010,17 @@ k_dot2(Reduce red, const double* __restrict__ a, const double* __restrict__ b,
        const double* __restrict__ c, const double* __restrict__ d, int64_t n,
        const int* __restrict__ skip) {
     if (skip && *skip) return;
-    double s0[kVecAccs] = {}, s1[kVecAccs] = {};
+    double s0 = 0.0, s1 = 0.0;
     if (c)
         vec_batched<4>(n, [&](int64_t i, double* e) { e[0] = a[i]; e[1] = b[i]; e[2] = c[i]; e[3] = d[i]; },
-                       [&](int64_t i, const double* e, int u) {
-                           s0[u % kVecAccs] += e[0] * e[1];
-                           s1[u % kVecAccs] += e[2] * e[3];
+                       [&](int64_t i, const double* e) {
+                           s0 += e[0] * e[1];
+                           s1 += e[2] * e[3];
                        });
     else
         vec_batched<2>(n, [&](int64_t i, double* e) { e[0] = a[i]; e[1] = b[i]; },
-                       [&](int64_t i, const double* e, int u) { s0[u % kVecAccs] += e[0] * e[1]; });
-    reduce_finalize<2>(red, acc_total(s0), acc_total(s1));
+                       [&](int64_t i, const double* e) { s0 += e[0] * e[1]; });
+    reduce_finalize<2>(red, s0, s1);
 }
 
 // Coarsest level: x = A_L^{-1} f, one warp per row of the dense inverse.
