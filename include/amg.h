@@ -88,7 +88,9 @@ typedef struct {
                               programmatic dependent launch (process-wide setting, applied
                               at each call that launches work).  Off by default: measured
                               slower in the solve's CUDA graph (150^3 FP64 8.72 against
-                              8.62 ms, 200^3 variable coefficients 464 against 447 ms). */
+                              8.62 ms, 200^3 variable coefficients 464 against 447 ms).
+                              Products of matrices below 2^21 nonzeros (coarse levels)
+                              use it either way. */
     int use_tail;          /* [0] run the small coarse levels (below about 4 million nonzeros,
                               finest level excluded) as one cooperative launch with grid-wide
                               barriers; applies when npre = npost = 1.  Off by default: inside

@@ -78,6 +78,7 @@ constexpr int kTileNnz = 2048;
 constexpr int kLongTileNnz = 4096;  // long-row tiles of the streaming engine (at most 128 rows)
 constexpr int kConsumers = 256;  // consumer threads per CTA of the streaming engine
 constexpr int kBlockRowNnz = 2048;  // long-row engine: rows this long or shorter never take a whole block
+constexpr int64_t kPdlAlwaysNnz = (int64_t)1 << 21;  // products below this size always use programmatic dependent launch
 
 struct DevCsr {
     int32_t nrows = 0, ncols = 0;
