@@ -197,16 +197,6 @@ amg_status amg_get_level_matrix(const amg_handle *h, int level, int which, int32
  * levels >= 1 only, the bfloat16-stored one not at all.) */
 amg_status amg_fused_restriction_nnz(const amg_handle *h, int level, int64_t *nnz);
 
-/* *on = 1 if the products with level matrix `which` (0 = A_l, 1 = P_l,
- * 2 = R_l, 3 = M_l) of level l stream 16-bit column offsets: each tile's
- * columns as offsets from the tile's smallest column, 10 bytes a float64
- * nonzero instead of 12.  The set-up makes them for float64 hierarchies
- * where every tile of the matrix spans fewer than 65,536 columns; other
- * matrices stream int32 columns.  Results are the same either way.  (A data
- * layout of this library for the products of Sec. 3 "Backends"; *on = 0
- * for a matrix the level does not have.) */
-amg_status amg_level_column_offsets(const amg_handle *h, int level, int which, int *on);
-
 /* Aggregate id of every row of level l (host array of rows[l] entries);
  * INVALID_ARG on the coarsest level. */
 amg_status amg_get_aggregates(const amg_handle *h, int level, int32_t *agg);

@@ -86,7 +86,6 @@ _sigs = {
     "amg_last_launch_count": [_VP, C.POINTER(_I64)],
     "amg_hierarchy_bytes": [_VP, C.POINTER(_D)],
     "amg_fused_restriction_nnz": [_VP, _I, C.POINTER(_I64)],
-    "amg_level_column_offsets": [_VP, _I, _I, C.POINTER(_I)],
     "amg_batch_bytes": [_VP, _VP],
     "amg_server_solve_bytes": [_VP, C.POINTER(_D)],
     "amg_last_solve_mode": [_VP, C.POINTER(_I), C.POINTER(_I)],
@@ -243,15 +242,6 @@ def amg_fused_restriction_nnz(h, level) -> int:
     v = C.c_int64()
     _check(_lib.amg_fused_restriction_nnz(h, level, C.byref(v)), "amg_fused_restriction_nnz")
     return v.value
-
-
-def amg_level_column_offsets(h, level, which) -> bool:
-    """which in {'A','P','R','M'}: whether the level's products with that
-    matrix stream 16-bit column offsets."""
-    v = C.c_int()
-    w = {"A": 0, "P": 1, "R": 2, "M": 3}[which]
-    _check(_lib.amg_level_column_offsets(h, level, w, C.byref(v)), "amg_level_column_offsets")
-    return bool(v.value)
 
 
 def amg_get_level_matrix(h, level, which):

@@ -78,7 +78,6 @@ constexpr int kTileNnz = 2048;
 constexpr int kLongTileNnz = 4096;  // long-row tiles of the streaming engine (at most 128 rows)
 constexpr int kConsumers = 256;  // consumer threads per CTA of the streaming engine
 constexpr int kBlockRowNnz = 2048;  // long-row engine: rows this long or shorter never take a whole block
-constexpr bool kColumnOffsets = true;  // 16-bit column offsets for float64 tiles that span < 65,536 columns
 constexpr int64_t kPdlAlwaysNnz = (int64_t)1 << 21;  // products below this size always use programmatic dependent launch
 
 struct DevCsr {
@@ -91,11 +90,6 @@ struct DevCsr {
     int32_t* blk = nullptr;  // row-block schedule (row-chunk engine)
     int32_t nblk = 0;
     int2* tiles = nullptr;   // streaming-engine tiles {first row, first nonzero}, ntiles + 1
-    // float64 hierarchies, where every tile spans fewer than 65,536 columns:
-    // each column as a 16-bit offset from its tile's smallest column
-    // (nnz + kPad entries), and that base column per tile (ntiles)
-    uint16_t* col16 = nullptr;
-    int32_t* tile_base = nullptr;
     int32_t ntiles = 0;      // 0: some row is longer than a tile, use the row-chunk engine
     int32_t vw = 1;          // lanes per row in the streaming engine
     int32_t rows_cap = 256;  // most rows in one tile (256, or 512 for P and R; 128 for long-row tiles)
@@ -222,8 +216,6 @@ void launch_prolong_pre_f32(const DevCsr& P, const float* d, const float* f, con
                             const int* skip, cudaStream_t s);
 
 // vector kernels
-bool tile_column_spans(const DevCsr& D, int32_t* base, int* flag, cudaStream_t s);
-void launch_col16(const DevCsr& D, const int32_t* base, uint16_t* col16, cudaStream_t s);
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s);
 void launch_cg_pupdate(KState* st, const double* z, double* p, double* x, int64_t n, cudaStream_t s);
 void launch_cg_xfinal(KState* st, const double* p, double* x, int64_t n, cudaStream_t s);

@@ -393,17 +393,6 @@ amg_status amg_fused_restriction_nnz(const amg_handle* h, int level, int64_t* nn
     });
 }
 
-amg_status amg_level_column_offsets(const amg_handle* h, int level, int which, int* on) {
-    return guarded([&]() -> amg_status {
-        const Level& L = level_of(h, level);
-        if (!on) fail(AMG_ERR_INVALID_ARG, "null output");
-        const DevCsr* D = which == 0 ? &L.A : which == 1 ? &L.P : which == 2 ? &L.R : which == 3 ? &L.M : nullptr;
-        if (!D) fail(AMG_ERR_INVALID_ARG, "which must be 0 (A), 1 (P), 2 (R) or 3 (M)");
-        *on = D->col16 ? 1 : 0;
-        return AMG_OK;
-    });
-}
-
 amg_status amg_hierarchy_bytes(const amg_handle* h, double* bytes_per_iteration) {
     return guarded([&]() -> amg_status {
         if (!h || !bytes_per_iteration) fail(AMG_ERR_INVALID_ARG, "null argument");

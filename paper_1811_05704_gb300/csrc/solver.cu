@@ -119,20 +119,6 @@ static void schedule(amg_handle* h, const std::vector<int32_t>& ptr, DevCsr& D, 
         int32_t* t = halloc<int32_t>(h, tiles.size());
         AMG_CUDA(cudaMemcpyAsync(t, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
         D.tiles = reinterpret_cast<int2*>(t);
-        // float64 hierarchies stream 16-bit column offsets from each tile's
-        // smallest column where every tile spans fewer than 65,536 columns:
-        // 10 bytes a nonzero instead of 12 (on 150^3 Poisson the finest and
-        // first coarse A, the prolongations and every matrix from level 2;
-        // not the fused restriction operators of levels 0-1)
-        if (kColumnOffsets && h->prm.precision == AMG_PRECISION_FP64) {
-            int32_t* base = halloc<int32_t>(h, D.ntiles);
-            int* flag = halloc<int>(h, 1);
-            if (tile_column_spans(D, base, flag, h->stream)) {
-                D.col16 = halloc<uint16_t>(h, D.nnz + kPad);
-                launch_col16(D, base, D.col16, h->stream);
-                D.tile_base = base;
-            }
-        }
     }
 }
 

@@ -65,13 +65,10 @@ __host__ __device__ constexpr int stream_ctas() { return sizeof(VT) >= 8 ? 3 : k
 __device__ int g_dev_err;  // bit 2: a pipeline wait gave up (see mbar_wait)
 
 // Nonzero spans are copied from a start rounded down, and to an end rounded
-// up, to a multiple of nz_align elements, so that both the column indices
-// (CT: int32, or uint16 offsets from the tile's base column) and the values
-// start and end on 16-byte boundaries.
-template <typename VT, typename CT = int32_t>
-__host__ __device__ constexpr int nz_align() {
-    return (16 / (int)sizeof(VT)) > (16 / (int)sizeof(CT)) ? 16 / (int)sizeof(VT) : 16 / (int)sizeof(CT);
-}
+// up, to a multiple of nz_align elements, so that both the column indices and
+// the values start and end on 16-byte boundaries.
+template <typename VT>
+__host__ __device__ constexpr int nz_align() { return sizeof(VT) >= 4 ? 4 : 16 / (int)sizeof(VT); }
 
 // Bytes per element of an epilogue's row-indexed vector k in shared memory:
 // the epilogue's vslot(k) if it declares one (it must be at least vbytes(k)
@@ -85,14 +82,14 @@ struct VecSlots<Epi, std::void_t<decltype(Epi::vslot(0))>> {
     __host__ __device__ static constexpr int at(int k) { return Epi::vslot(k); }
 };
 
-template <typename VT, int RMAX, typename Epi, typename CT = int32_t>
+template <typename VT, int RMAX, typename Epi>
 struct StreamLayout {
     static constexpr int NV = Epi::nvec;
     static constexpr int rp_n = RMAX + 8;       // row pointers of the tile (+ alignment slack)
-    static constexpr int nz_n = tile_nnz<RMAX>() + 2 * nz_align<VT, CT>();  // nonzeros of the tile (+ alignment slack)
+    static constexpr int nz_n = tile_nnz<RMAX>() + 2 * nz_align<VT>();  // nonzeros of the tile (+ alignment slack)
     static constexpr int vec_n = RMAX + 8;      // rows of a row-indexed vector slice (+ alignment slack)
     static constexpr size_t rp_bytes = (size_t)rp_n * 4;
-    static constexpr size_t col_bytes = (size_t)nz_n * sizeof(CT);
+    static constexpr size_t col_bytes = (size_t)nz_n * 4;
     static constexpr size_t val_bytes = (size_t)nz_n * sizeof(VT);
     __host__ __device__ static constexpr size_t vec_bytes(int k) {
         return ((size_t)vec_n * VecSlots<Epi>::at(k) + 15) / 16 * 16;
@@ -170,18 +167,18 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 constexpr int kGatherBatch = 4;
 
 // sum -/+ the products of nonzeros k, k + vw, ... < ke, in that order; the
-// columns (cbase + cs[k]), values and gathered operands of kGatherBatch
-// nonzeros at a time are loaded before any is accumulated.
-template <int SIGN, typename acc_t, typename VT, typename CT, typename Epi>
-__device__ __forceinline__ acc_t row_batched(acc_t sum, int k, int ke, int vw, const VT* vs, const CT* cs,
-                                             int cbase, const Epi& epi) {
+// columns, values and gathered operands of kGatherBatch nonzeros at a time
+// are loaded before any is accumulated.
+template <int SIGN, typename acc_t, typename VT, typename Epi>
+__device__ __forceinline__ acc_t row_batched(acc_t sum, int k, int ke, int vw, const VT* vs, const int* cs,
+                                             const Epi& epi) {
     for (; k < ke; k += kGatherBatch * vw) {
         int c[kGatherBatch];
         acc_t a[kGatherBatch], x[kGatherBatch];
 #pragma unroll
         for (int u = 0; u < kGatherBatch; ++u) {
             const bool in = k + u * vw < ke;
-            c[u] = in ? cbase + (int)cs[k + u * vw] : 0;
+            c[u] = in ? cs[k + u * vw] : 0;
             a[u] = in ? (acc_t)vs[k + u * vw] : acc_t(0);
         }
 #pragma unroll
@@ -197,27 +194,22 @@ __device__ __forceinline__ acc_t row_batched(acc_t sum, int k, int ke, int vw, c
     return sum;
 }
 
-// CT: the column type of the copied tiles -- int32 columns, or uint16 offsets
-// from the tile's base column (tile_base, one per tile) for matrices whose
-// tiles each span fewer than 65,536 columns: 2 bytes less per nonzero.
-template <typename VT, typename Epi, int RMAX, typename CT = int32_t>
+template <typename VT, typename Epi, int RMAX>
 __global__ void __launch_bounds__(kCons + 32, stream_ctas<VT>())
-k_stream(const int32_t* __restrict__ ptr, const CT* __restrict__ col,
+k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
          const VT* __restrict__ val, const int2* __restrict__ tiles, int ntiles, int vw, Epi epi,
-         Reduce red, const int* __restrict__ skip, const int32_t* __restrict__ tile_base) {
+         Reduce red, const int* __restrict__ skip) {
     using acc_t = typename Epi::acc_t;
     constexpr int NV = Epi::nvec;
-    constexpr bool kOff = std::is_same<CT, uint16_t>::value;  // columns as offsets from a tile base
-    using L = StreamLayout<VT, RMAX, Epi, CT>;
+    using L = StreamLayout<VT, RMAX, Epi>;
     constexpr int kStages = stages<VT, RMAX>();  // at most 3: the 128-byte header holds their barriers
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* empty = full + kStages;
     int4* info = reinterpret_cast<int4*>(sm + 64);
-    int* tbase = reinterpret_cast<int*>(sm + 112);  // base column of each stage's tile (kOff)
     auto stage_of = [&](int s) { return sm + L::header + s * L::stage; };
     auto rp_of = [&](int s) { return reinterpret_cast<int*>(stage_of(s)); };
-    auto col_of = [&](int s) { return reinterpret_cast<CT*>(stage_of(s) + L::rp_bytes); };
+    auto col_of = [&](int s) { return reinterpret_cast<int*>(stage_of(s) + L::rp_bytes); };
     auto val_of = [&](int s) { return reinterpret_cast<VT*>(stage_of(s) + L::rp_bytes + L::col_bytes); };
     auto vec_of = [&](int s, int k) {
         return stage_of(s) + L::rp_bytes + L::col_bytes + L::val_bytes + L::vec_off(k);
@@ -252,18 +244,17 @@ k_stream(const int32_t* __restrict__ ptr, const CT* __restrict__ col,
             auto issue = [&](int i) {
                 const int s = i % kStages;
                 const int ar = cur.x & ~3, re = (nxt.x + 1 + 3) & ~3, vre = (nxt.x + 3) & ~3;
-                constexpr int na = nz_align<VT, CT>();
+                constexpr int na = nz_align<VT>();
                 const int ak = cur.y & ~(na - 1), ke = (nxt.y + na - 1) & ~(na - 1);
                 info[s] = make_int4(cur.x, nxt.x, ar, ak);
-                if constexpr (kOff) tbase[s] = __ldg(tile_base + t0 + i);
                 const uint32_t brp = (uint32_t)(re - ar) * 4u;
                 const uint32_t bnz = (uint32_t)(ke - ak);
-                uint32_t bytes = brp + bnz * ((uint32_t)sizeof(CT) + (uint32_t)sizeof(VT));
+                uint32_t bytes = brp + bnz * (4u + (uint32_t)sizeof(VT));
                 for (int k = 0; k < NV; ++k) bytes += (uint32_t)(vre - ar) * (uint32_t)epi.vbytes(k);
                 mbar_arrive_tx(&full[s], bytes);
                 bulk_g2s(rp_of(s), ptr + ar, brp, &full[s], pol);
                 if (bnz) {
-                    bulk_g2s(col_of(s), col + ak, bnz * (uint32_t)sizeof(CT), &full[s], pol);
+                    bulk_g2s(col_of(s), col + ak, bnz * 4u, &full[s], pol);
                     bulk_g2s(val_of(s), val + ak, bnz * (uint32_t)sizeof(VT), &full[s], pol);
                 }
                 for (int k = 0; k < NV; ++k) {
@@ -301,13 +292,7 @@ k_stream(const int32_t* __restrict__ ptr, const CT* __restrict__ col,
             if (!stop) {
                 const int4 inf = info[s];
                 const int* rp = rp_of(s);
-                const CT* cs = col_of(s);
-                const int cbase = kOff ? tbase[s] : 0;
-                // column of staged nonzero k
-                auto colat = [&](int k) -> int {
-                    if constexpr (kOff) return cbase + (int)cs[k];
-                    else return cs[k];
-                };
+                const int* cs = col_of(s);
                 const VT* vs = val_of(s);
                 VecTile vt;
 #pragma unroll
@@ -339,11 +324,11 @@ k_stream(const int32_t* __restrict__ ptr, const CT* __restrict__ col,
                             const bool a = kA < keA, b = kB < keB;
                             if (!a && !b) break;
                             if constexpr (Seeding<Epi>::sign < 0) {
-                                if (a) sumA -= (acc_t)vs[kA] * epi.xg(colat(kA));
-                                if (b) sumB -= (acc_t)vs[kB] * epi.xg(colat(kB));
+                                if (a) sumA -= (acc_t)vs[kA] * epi.xg(cs[kA]);
+                                if (b) sumB -= (acc_t)vs[kB] * epi.xg(cs[kB]);
                             } else {
-                                if (a) sumA += (acc_t)vs[kA] * epi.xg(colat(kA));
-                                if (b) sumB += (acc_t)vs[kB] * epi.xg(colat(kB));
+                                if (a) sumA += (acc_t)vs[kA] * epi.xg(cs[kA]);
+                                if (b) sumB += (acc_t)vs[kB] * epi.xg(cs[kB]);
                             }
                             kA += vw;
                             kB += vw;
@@ -375,13 +360,13 @@ k_stream(const int32_t* __restrict__ ptr, const CT* __restrict__ col,
                             // of up to kGatherBatch of its nonzeros, issues
                             // their gathers together, then accumulates them
                             // in order (the same order as one at a time)
-                            sum = row_batched<Seeding<Epi>::sign>(sum, kb + lane, ke, vw, vs, cs, cbase, epi);
+                            sum = row_batched<Seeding<Epi>::sign>(sum, kb + lane, ke, vw, vs, cs, epi);
                         } else if constexpr (Seeding<Epi>::sign < 0) {
 #pragma unroll 4
-                            for (int k = kb + lane; k < ke; k += vw) sum -= (acc_t)vs[k] * epi.xg(colat(k));
+                            for (int k = kb + lane; k < ke; k += vw) sum -= (acc_t)vs[k] * epi.xg(cs[k]);
                         } else {
 #pragma unroll 4
-                            for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(colat(k));
+                            for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
                         }
                     }
                     for (int o = vw >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, vw);
@@ -676,11 +661,10 @@ int read_and_clear_dev_err() {
     return v;
 }
 
-template <typename VT, typename Epi, int RMAX, typename CT = int32_t>
+template <typename VT, typename Epi, int RMAX>
 static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& red,
                           const int* skip, cudaStream_t s) {
-    constexpr bool kOff = std::is_same<CT, uint16_t>::value;
-    const size_t smem = StreamLayout<VT, RMAX, Epi, CT>::total;
+    const size_t smem = StreamLayout<VT, RMAX, Epi>::total;
     // once per template instance (thread-safe static initialisation): the
     // shared-memory limit, and the CTAs per SM the grid is sized for -- the
     // resident count the device reports, at most stream_ctas<VT>(), so that
@@ -688,13 +672,13 @@ static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const 
     // CTAs per SM ask for the largest shared-memory carveout; the float64
     // kernels keep the default, whose larger L1 serves their gathers.
     static const int ctas = [smem] {
-        AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         if (stream_ctas<VT>() > 2)
-            AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX, CT>,
+            AMG_CUDA(cudaFuncSetAttribute(k_stream<VT, Epi, RMAX>,
                                           cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         int per_sm = 0;
-        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream<VT, Epi, RMAX, CT>, kCons + 32,
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream<VT, Epi, RMAX>, kCons + 32,
                                                                smem));
         return std::max(1, std::min(per_sm, stream_ctas<VT>()));
     }();
@@ -715,12 +699,8 @@ static void launch_stream(const DevCsr& A, const VT* val, const Epi& epi, const 
     // Poisson, FP64: 8.384 -> 8.363 ms with it below 2^21 nonzeros, 8.368 ms
     // below 2^23, slower for every kernel (8.72 against 8.62 ms).
     cfg.numAttrs = (g_pdl || A.nnz < kPdlAlwaysNnz) ? 1 : 0;
-    const CT* col;
-    if constexpr (kOff) col = A.col16;
-    else col = A.col;
-    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_stream<VT, Epi, RMAX, CT>, (const int32_t*)A.ptr, col, val,
-                                (const int2*)A.tiles, (int)A.ntiles, (int)A.vw, epi, red, skip,
-                                (const int32_t*)A.tile_base));
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_stream<VT, Epi, RMAX>, (const int32_t*)A.ptr, (const int32_t*)A.col,
+                                val, (const int2*)A.tiles, (int)A.ntiles, (int)A.vw, epi, red, skip));
 }
 
 template <typename VT, typename Epi>
@@ -748,15 +728,6 @@ static void run(const DevCsr& A, const VT* val, const Epi& epi, const Reduce& re
                 const int* skip, cudaStream_t s) {
     if (A.nrows == 0) return;
     if (A.tiles) {
-        // float64 values read 16-bit column offsets where the set-up made them
-        if constexpr (sizeof(VT) >= 8) {
-            if (A.col16) {
-                if (A.nz_cap == kLongTileNnz) launch_stream<VT, Epi, 128, uint16_t>(A, val, epi, red, skip, s);
-                else if (A.rows_cap <= 256) launch_stream<VT, Epi, 256, uint16_t>(A, val, epi, red, skip, s);
-                else launch_stream<VT, Epi, 512, uint16_t>(A, val, epi, red, skip, s);
-                return;
-            }
-        }
         if (A.nz_cap == kLongTileNnz) launch_stream<VT, Epi, 128>(A, val, epi, red, skip, s);
         else if (A.rows_cap <= 256) launch_stream<VT, Epi, 256>(A, val, epi, red, skip, s);
         else launch_stream<VT, Epi, 512>(A, val, epi, red, skip, s);
@@ -1130,75 +1101,6 @@ static int vec_grid_k(int64_t n) {
     const int64_t per = (int64_t)kThreads * kVecBatch;
     const int64_t g = std::min<int64_t>((n + per - 1) / per, stream_grid(1 << 30, per_sm));
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, vec_grid(n)));  // within the reduction buffer
-}
-
-// ------------------------------------------- 16-bit column offsets (set-up)
-// Smallest and largest column of each streaming tile: base[t] = the smallest
-// (0 for a tile without nonzeros); *too_wide |= 1 if a tile spans more than
-// 65,535 columns.
-__global__ void __launch_bounds__(kThreads)
-k_tile_span(const int2* __restrict__ tiles, int ntiles, const int32_t* __restrict__ col,
-            int32_t* __restrict__ base, int* __restrict__ too_wide) {
-    __shared__ int smin[kThreads / 32], smax[kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int k0 = tiles[t].y, k1 = tiles[t + 1].y;
-        int mn = 0x7fffffff, mx = 0;
-        for (int k = k0 + (int)threadIdx.x; k < k1; k += kThreads) {
-            const int c = col[k];
-            mn = min(mn, c);
-            mx = max(mx, c);
-        }
-        mn = __reduce_min_sync(0xffffffffu, mn);
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) {
-            smin[warp] = mn;
-            smax[warp] = mx;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < kThreads / 32; ++w) {
-                mn = min(mn, smin[w]);
-                mx = max(mx, smax[w]);
-            }
-            base[t] = k1 > k0 ? mn : 0;
-            if (k1 > k0 && mx - mn > 65535) atomicOr(too_wide, 1);
-        }
-        __syncthreads();
-    }
-}
-
-// col16[k] = col[k] - base[tile of k]
-__global__ void __launch_bounds__(kThreads)
-k_col16(const int2* __restrict__ tiles, int ntiles, const int32_t* __restrict__ col,
-        const int32_t* __restrict__ base, uint16_t* __restrict__ col16) {
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int k0 = tiles[t].y, k1 = tiles[t + 1].y, b = base[t];
-        for (int k = k0 + (int)threadIdx.x; k < k1; k += kThreads) col16[k] = (uint16_t)(col[k] - b);
-    }
-}
-
-// Tile base columns of D's streaming tiles into base (ntiles entries); true if
-// every tile spans at most 65,535 columns.  flag: one device int of scratch.
-// Synchronises the stream (the set-up reads the answer).
-bool tile_column_spans(const DevCsr& D, int32_t* base, int* flag, cudaStream_t s) {
-    if (D.ntiles <= 0) return false;
-    AMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
-    const int grid = std::min(D.ntiles, 152 * 8);
-    k_tile_span<<<grid, kThreads, 0, s>>>(D.tiles, D.ntiles, D.col, base, flag);
-    AMG_CUDA(cudaGetLastError());
-    int wide = 1;
-    AMG_CUDA(cudaMemcpyAsync(&wide, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_CUDA(cudaStreamSynchronize(s));
-    return wide == 0;
-}
-
-// col16 (nnz + kPad entries, zeroed here) from D.col and the tile bases.
-void launch_col16(const DevCsr& D, const int32_t* base, uint16_t* col16, cudaStream_t s) {
-    AMG_CUDA(cudaMemsetAsync(col16, 0, (size_t)(D.nnz + kPad) * sizeof(uint16_t), s));
-    const int grid = std::min(D.ntiles, 152 * 8);
-    k_col16<<<grid, kThreads, 0, s>>>(D.tiles, D.ntiles, D.col, base, col16);
-    AMG_CUDA(cudaGetLastError());
 }
 
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {

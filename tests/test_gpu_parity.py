@@ -280,60 +280,6 @@ def test_solve_matches_oracle(amg, torch_dev, case):
     S.close()
 
 
-def _laplace1d_long_range(n):
-    """1D Laplacian [-1 2 -1] on n rows plus a symmetric coupling -0.5
-    between rows 0 and n - 1: the tiles that hold those rows span n - 1
-    columns (diagonally dominant, so SPD)."""
-    rows, cols, vals = [], [], []
-    for i in range(n):
-        nb = [(i, 2.0)]
-        if i > 0:
-            nb.append((i - 1, -1.0))
-        if i < n - 1:
-            nb.append((i + 1, -1.0))
-        if i == 0:
-            nb.append((n - 1, -0.5))
-        if i == n - 1:
-            nb.append((0, -0.5))
-        for c, v in sorted(nb):
-            rows.append(i)
-            cols.append(c)
-            vals.append(v)
-    ptr = np.zeros(n + 1, np.int32)
-    np.add.at(ptr, np.asarray(rows) + 1, 1)
-    return gen.Csr(n, np.cumsum(ptr).astype(np.int32), np.asarray(cols, np.int32), np.asarray(vals))
-
-
-def test_column_offsets_and_their_fallback(amg, torch_dev):
-    """Float64 hierarchies stream 16-bit column offsets for the matrices whose
-    tiles each span fewer than 65,536 columns and int32 columns for the
-    others; float32 hierarchies always stream int32 columns.  Either way the
-    solve is the oracle's (iterations +-1, x within 1e-6)."""
-    cases = [(gen.poisson3d(40), {}), (_laplace1d_long_range(70000), {"coarse_enough": 300})]
-    for k, (A, kw) in enumerate(cases):
-        S, H = both(amg, A, **kw)
-        on = amg.amg_level_column_offsets(S.handle, 0, "A")
-        if k == 0:
-            # 40^3: a tile of A_0 spans about 2 * 40^2 + 256 columns
-            assert on and amg.amg_level_column_offsets(S.handle, 0, "P")
-        else:
-            # the tile holding row 0 spans n - 1 columns; P_0 maps rows to aggregates
-            assert not on and amg.amg_level_column_offsets(S.handle, 0, "P")
-        f, _ = gen.rhs_from_solution(A, 5)
-        x = t(torch_dev, np.zeros(A.n))
-        st, it, rr = S.solve(t(torch_dev, f), x, rtol=1e-8, maxiter=300)
-        xo, ito, rro, sto = H.cg(f, rtol=1e-8, maxiter=300)
-        xs = x.cpu().numpy()
-        assert st == 0 and sto == 0 and rr <= 1e-8
-        assert abs(it - ito) <= 1, (it, ito)
-        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
-        S.close()
-    A = gen.poisson3d(40)
-    S = amg.Solver(A.n, A.row_ptr, A.col, A.val, precision=1)
-    assert not amg.amg_level_column_offsets(S.handle, 0, "A")
-    S.close()
-
-
 @pytest.mark.parametrize("case", ["poisson32", "varcoef20", "convdiff18"])
 def test_fused_restriction_on_and_off_match_oracle(amg, torch_dev, case):
     """The solve with the fused restriction operator (the default) and
