@@ -166,11 +166,6 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 constexpr int kGatherBatch = 4;
 
-// Unrolling of a float64 lane's loop over its nonzeros, so many gathers in
-// flight: 8 in long-row tiles (rows of 32-300 nonzeros, 8-20 a lane), else 4.
-template <int RMAX>
-__host__ __device__ constexpr int kFp64Unroll() { return RMAX == 128 ? 8 : 4; }
-
 // sum -/+ the products of nonzeros k, k + vw, ... < ke, in that order; the
 // columns, values and gathered operands of kGatherBatch nonzeros at a time
 // are loaded before any is accumulated.
@@ -367,10 +362,10 @@ k_stream(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                             // in order (the same order as one at a time)
                             sum = row_batched<Seeding<Epi>::sign>(sum, kb + lane, ke, vw, vs, cs, epi);
                         } else if constexpr (Seeding<Epi>::sign < 0) {
-#pragma unroll (kFp64Unroll<RMAX>())
+#pragma unroll 4
                             for (int k = kb + lane; k < ke; k += vw) sum -= (acc_t)vs[k] * epi.xg(cs[k]);
                         } else {
-#pragma unroll (kFp64Unroll<RMAX>())
+#pragma unroll 4
                             for (int k = kb + lane; k < ke; k += vw) sum += (acc_t)vs[k] * epi.xg(cs[k]);
                         }
                     }
