@@ -283,21 +283,35 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def spmv_code_digest():
+    """SHA-256 (first 16 hex digits) of csrc/spmv.cu's code: every line with
+    its // comment removed and trailing blanks stripped, blank lines dropped,
+    so that an edit of comments alone keeps the digest."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1811_05704_gb300", "csrc", "spmv.cu")
+    lines = []
+    for line in open(src, encoding="utf-8").read().splitlines():
+        i = line.find("//")
+        if i >= 0:
+            line = line[:i]
+        line = line.rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def committed_traffic(kernel_class):
     """Per-launch DRAM bytes from the committed ncu summary of this kernel, or
-    None if the summary is missing or the kernel source changed since."""
-    import hashlib
+    None if the summary is missing or the kernel code changed since."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel_class}_poisson150.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_1811_05704_gb300", "csrc", "spmv.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     fields = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    if fields.get("spmv_cu_sha256_16") != digest:
+    if fields.get("spmv_cu_code_sha256_16") != spmv_code_digest():
         return None
     try:
         return float(fields["dram_bytes_per_launch"])

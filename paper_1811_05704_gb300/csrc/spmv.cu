@@ -876,9 +876,10 @@ __global__ void k_fill(double* x, double v, int64_t n) {
 // Vector kernels run a grid-stride loop that takes kVecBatch elements a
 // thread at a time (i, i + stride, ...): ld(i, v) loads element i's inputs
 // for all of them before op(i, v) uses any, so that a thread keeps
-// kVecBatch times the loads in flight (one element at a time left these
-// kernels at about half the HBM bandwidth).  op runs in element order, so
-// sums accumulate in the same order as one element at a time.
+// kVecBatch times the loads in flight.  op runs in element order, so sums
+// accumulate in the same order as one element at a time.  (On 150^3 the
+// update kernels measured about the same either way: they are held by the
+// float64 pipe, two operations an element, and the reduction at their end.)
 constexpr int kVecBatch = 4;
 template <int NV, typename Ld, typename Op>
 __device__ __forceinline__ void vec_batched(int64_t n, Ld ld, Op op) {
